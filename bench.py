@@ -1,0 +1,453 @@
+#!/usr/bin/env python3
+"""Benchmark of batched seamless filtered Htex lookups (libhtex, GB300).
+
+Default workload (one step = one htex_lookup over every query of the
+batch): the asset-scale mesh, an open cylinder of 256 quads around and 460
+rows with about 30% of quads split into triangles and about 5% of faces
+merged into 5- to 8-gons (522,126 halfedges, 261k edges), one 64x64 RGBA8
+UNORM texture per edge with its mip chain (5.7 GB), 16,777,216 queries per
+GPU with uniform halfedge ids and barycentrics and log-uniform footprints
+2^-8..1 (trilinear).  Inputs are seeded and synthetic.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead, on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filtered Htex lookups/s"
+UNIT = "lookups/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--queries", type=int, default=1 << 24)
+    p.add_argument("--bin", action="store_true", help="reorder queries by halfedge first")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- workload
+
+def asset_inputs(rank: int, nq: int):
+    import htex_synth as syn
+    fs, fv, V, _ = syn.cylinder()
+    return fs, fv, V, syn.queries(int(fs.sum()), nq, seed=1000 + rank, footprint="loguniform")
+
+
+def workload_config(H, E, nq, flags_name):
+    return {
+        "workload": "asset-scale open cylinder 256x460 quads with splits and merges; "
+                    "64x64 RGBA8 UNORM edge textures with mip chains; log-uniform footprints 2^-8..1",
+        "halfedges": int(H), "edges": int(E), "texel_format": "rgba8_unorm", "texture_res": 64,
+        "queries_per_gpu": int(nq), "lookup_flags": flags_name,
+        "l2": "inputs larger than L2: 256 MB queries, 256 MB outputs, 5.7 GB texels per step",
+    }
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2207_05618_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(os.path.basename(p).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, when it was
+    taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "lookup_asset_scale.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    t = re.search(rf"{kernel}_dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if m and t and m.group(1) == source_hash():
+        return float(t.group(1))
+    return None
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy kernel)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
+
+
+def algorithmic_bytes(he, n_uniform: int, qs, texel_bytes: int, sample: int = 1 << 20) -> float:
+    """Bytes one lookup must move, averaged over a sample of the queries:
+    the 16-byte query, the 16-byte output, the 16-byte lookup record of h,
+    and every texel tap with nonzero weight that falls inside its texture
+    (own, Next and Prev fetches, one or two levels each), texel_bytes each."""
+    h, u, v, f = (np.asarray(x)[:sample] for x in qs)
+    u = np.maximum(u.astype(np.float64), 0)
+    v = np.maximum(v.astype(np.float64), 0)
+    s = u + v
+    over = s > 1
+    u[over] /= s[over]
+    v[over] /= s[over]
+    with np.errstate(divide="ignore"):
+        lam = np.where(f > 0, np.log2(np.where(f > 0, f, 1.0)) + n_uniform, -1.0)
+    d = np.floor(lam)
+    taps = np.zeros(h.shape[0])
+    twin, nxt, prv = he["twin"], he["next"], he["prev"]
+    for g, a, b in ((h, u, v), (nxt[h], v, -u), (prv[h], -v, u)):
+        flip = g < twin[g]
+        x = np.where(flip, 1 - a, a)
+        y = np.where(flip, 1 - b, b)
+        single = ~(lam > 0) | (d >= n_uniform)
+        l0 = np.where(~(lam > 0), 0, np.minimum(d, n_uniform)).astype(np.int64)
+        for lev, active, w in ((l0, np.ones_like(single), np.where(single, 1.0, 1 - (lam - d))),
+                               (l0 + 1, ~single, lam - d)):
+            N = np.left_shift(1, np.clip(n_uniform - lev, 0, 30)).astype(np.float64)
+            sx, sy = x * N - 0.5, y * N - 0.5
+            i0, j0 = np.floor(sx), np.floor(sy)
+            ax, by = sx - i0, sy - j0
+            for di, wx in ((0, 1 - ax), (1, ax)):
+                for dj, wy in ((0, 1 - by), (1, by)):
+                    ii, jj = i0 + di, j0 + dj
+                    ok = (ii >= 0) & (ii < N) & (jj >= 0) & (jj < N) & (wx * wy * w > 0) & active
+                    taps += ok
+    return 48.0 + float(taps.mean()) * texel_bytes
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons, timestamped on receipt."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.samples = []
+        self.proc = None
+        sel = []
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            sel = ["-i", vis.split(",")[device_index]] if vis else ["-i", str(device_index)]
+        self.cmd = ["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                    "-lms", "100"]
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        def read():
+            for line in self.proc.stdout:
+                self.samples.append((time.time(), line.strip()))
+        self.thread = threading.Thread(target=read, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        sm, mx, reasons = [], [], set()
+        for ts, line in self.samples:
+            if not (t0 <= ts <= t1 + 0.15):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle sample
+
+def oracle_sample(nq_sample: int, seed: int = 7, slice_h: int = 4096):
+    """A bounded oracle workload: the same mesh, textures and query
+    distribution, with queries restricted to halfedges [0, slice_h) so the
+    oracle's FP64 copy of the touched textures fits host memory."""
+    import htex_synth as syn
+    import oracle
+    fs, fv, V, _ = syn.cylinder()
+    mo = oracle.mesh_from_faces(fs, fv, V)
+    log2n = np.full(mo.num_edges, 6, np.int32)
+    h, u, v, f = syn.queries(slice_h, nq_sample, seed=seed, footprint="loguniform")
+    hs = np.arange(slice_h)
+    edges = np.unique(np.concatenate([mo.edge[hs], mo.edge[mo.next[hs]], mo.edge[mo.prev[hs]]]))
+    keep = np.zeros(mo.num_edges, bool)
+    keep[edges] = True
+    rng = np.random.default_rng(21)
+    ln = np.where(keep, log2n, 0).astype(np.int32)
+    counts = (np.int64(1) << (2 * ln.astype(np.int64))) * 4
+    tex = np.frombuffer(rng.bytes(int(counts.sum())), np.uint8)
+    to = oracle.prepare_textures(mo, ln, tex, 4, "u8", oracle.BUILD_MIPS)
+    return mo, to, (h, u, v, f)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(budget_s: float):
+    """Oracle lookups/s on all host cores, sample sized to about budget_s."""
+    import oracle
+    cores = host_cores()
+    mo, to, qs = oracle_sample(1 << 21)
+    oracle.lookup(mo, to, tuple(x[:1 << 14] for x in qs), nthreads=cores)   # warm the caches
+    n = 0
+    t = time.perf_counter()
+    while True:                     # whole passes over the sample until the budget is spent
+        oracle.lookup(mo, to, qs, nthreads=cores)
+        n += qs[0].shape[0]
+        dt = time.perf_counter() - t
+        if dt >= budget_s:
+            break
+    return n / dt, cores, n, (mo, to, qs)
+
+
+# ---------------------------------------------------------------- reference
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = host_cores()
+    mo, to, qs = oracle_sample(1 << 21)
+    budget = max(0.05, 150.0 / max(args.steps + args.warmup, 1))
+    probe = 1 << 13
+    t = time.perf_counter()
+    oracle.lookup(mo, to, tuple(x[:probe] for x in qs), nthreads=cores)
+    rate = probe / max(time.perf_counter() - t, 1e-6)
+    n = int(min(qs[0].shape[0], max(1024, rate * budget)))
+    sub = tuple(x[:n] for x in qs)
+    for _ in range(args.warmup):
+        oracle.lookup(mo, to, sub, nthreads=cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.lookup(mo, to, sub, nthreads=cores)
+    dt = time.perf_counter() - t
+    value = n * args.steps / dt
+    cfg = workload_config(mo.H, mo.num_edges, n, "oracle")
+    sample = (f"{n} queries per step with h uniform on halfedges [0, 4096) of the asset, "
+              f"barycentrics and footprints as the workload; FP64 oracle on {cores} host threads")
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------- ours
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2207_05618_gb300 import build as b
+    if rank == 0:
+        b.build()
+    if dist:
+        dist.barrier()
+    import paper_2207_05618_gb300 as hx
+
+    nq = args.queries
+    fs, fv, V, qs = asset_inputs(rank, nq)
+    mesh = hx.Mesh(fs, fv, V)
+    log2n = np.full(mesh.E, 6, np.int32)
+    import htex_synth as syn
+    texels = syn.texels_u8(log2n, 4, seed=21)
+    tex = hx.Textures.upload(mesh, log2n, texels, 4, "u8", hx.BUILD_MIPS)
+    del texels
+    flags = hx.LOOKUP_BIN if args.bin else 0
+    q_host = torch.from_numpy(hx.pack_queries(*qs)).pin_memory()
+    q = q_host.cuda()
+    out = torch.empty((nq, 4), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    bytes_per_lookup = algorithmic_bytes(mesh.halfedges(), 6, qs, 4)
+
+    def step():
+        hx.lookup(tex, q, out=out, flags=flags, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for k in range(args.steps):
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t1 = time.time()
+    sampler.stop()
+    total_ms = starts[0].elapsed_time(ends[-1])
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = nq * args.steps * world / (total_ms / 1e3)
+    clocks = sampler.summary(t0, t1)
+
+    # end to end through the public API: pinned host queries in, host results out
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty((nq, 4), dtype=torch.float32).pin_memory()
+        def e2e_step():
+            q.copy_(q_host, non_blocking=True)
+            hx.lookup(tex, q, out=out, flags=flags, stream=stream)
+            out_host.copy_(out, non_blocking=True)
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ksteps = max(1, min(args.steps, 50))
+        e0.record(stream)
+        for _ in range(ksteps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        if dist:
+            tt = torch.tensor([ems], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": nq * ksteps * world / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(q_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4),
+               "steps": ksteps, "path": "pinned host -> cudaMemcpyAsync -> htex_lookup -> pinned host"}
+
+    # the spec streaming case: the closed cube, 16x16 RGBA FP32, 2^24 queries
+    cube = cube_stream(hx, torch, stream, args)
+
+    peak, peak_src = hbm_peak()
+    avg_ms = float(np.mean(launch_ms))
+    achieved = bytes_per_lookup * nq / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic("lookup"), "peak_source": peak_src,
+                "algorithmic_bytes_per_lookup": bytes_per_lookup, "kernel": "k_lookup_global<u8,4>",
+                "avg_launch_ms": avg_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, cores, n_s, _ = time_oracle(15.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_s} lookups (passes over 2,097,152 queries) with h uniform on halfedges "
+                         f"[0, 4096) of the asset, barycentrics "
+                         f"and footprints as the workload (the FP64 copy of all 5.7 GB of texels does not "
+                         f"fit host memory)"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(mesh.H, mesh.E, nq, "bin" if args.bin else "none"),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": args.steps * (1 if not args.bin else 4), "cube_stream": cube,
+            "source_hash": source_hash(),
+        }), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def cube_stream(hx, torch, stream, args):
+    """Closed cube, 12 textures 16x16 RGBA FP32 + mips, 2^24 queries at
+    level 0: 32 algorithmic bytes per lookup (query + output)."""
+    import htex_synth as syn
+    fs, fv, V, _ = syn.cube()
+    mesh = hx.Mesh(fs, fv, V)
+    log2n = np.full(mesh.E, 4, np.int32)
+    tex = hx.Textures.upload(mesh, log2n, syn.texels_f32(log2n, 4, seed=1), 4, "f32", hx.BUILD_MIPS)
+    res = {}
+    for name, n in (("batched_2^24", 1 << 24), ("single_65536", 65536)):
+        q = torch.from_numpy(hx.pack_queries(*syn.queries(mesh.H, n, seed=2))).cuda()
+        out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        for _ in range(5):
+            hx.lookup(tex, q, out=out, stream=stream)
+        reps = 50
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            hx.lookup(tex, q, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"lookups_per_s": n / (ms / 1e3), "ms": ms, "gbs": 32.0 * n / (ms / 1e3) / 1e9}
+    peak, _ = hbm_peak()
+    res["batched_2^24"]["frac_of_hbm"] = res["batched_2^24"]["gbs"] / peak
+    tex.close()
+    return res
+
+
+if __name__ == "__main__":
+    main()

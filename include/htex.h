@@ -1,0 +1,257 @@
+/*
+ * htex.h — C ABI of libhtex, batched seamless filtered lookups on
+ * per-halfedge textures (Htex: Barbier & Dupuy, "Per-Halfedge Texturing
+ * for Arbitrary Mesh Topologies", 2022), for NVIDIA GB300 (sm_103a).
+ *
+ * The problem, as the paper states it: a polygon mesh given as halfedges
+ * (Section 2, Fig. 2: operators Twin, Next, Prev, Vert, Edge, Face) carries
+ * one square texture per edge, i.e. per intrinsic quad formed by a halfedge
+ * and its twin (Section 3.2, Section 4.3).  A query names a halfedge h and
+ * barycentric coordinates (u, v) on the intrinsic triangle of h (Section
+ * 4.2); its value blends three border-normalised fetches: the quad of h at
+ * (u, v), the quad of Next(h) at (v, -u) and the quad of Prev(h) at (-v, u),
+ * each mapped by Alg. 2 (Alg. 3).
+ *
+ * Conventions for every call:
+ *   - Return values are htex_status codes; no call throws or aborts.
+ *     Argument errors are reported synchronously, before any device work.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device (e.g. torch.Tensor.data_ptr()).
+ *   - The library owns the memory behind htex_mesh and htex_textures and
+ *     frees it in the matching *_destroy call.  The caller owns every
+ *     buffer it passes in.
+ *   - Device work is asynchronous on the given stream (NULL = the legacy
+ *     default stream) unless the call says it synchronises.
+ *   - A htex_stream is a cudaStream_t (the same handle type), spelled
+ *     without CUDA headers.
+ *   - Per-query problems (h out of range, u or v not finite) do not fail a
+ *     call: that query's outputs are NaN and, when a device status word is
+ *     given, it is incremented once per such query.
+ */
+#ifndef HTEX_H
+#define HTEX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HTEX_OK = 0,
+    HTEX_ERR_INVALID_ARG = 1,        /* null pointer, bad size, bad enum value        */
+    HTEX_ERR_NONMANIFOLD = 2,        /* a directed edge used twice, or twins disagree */
+    HTEX_ERR_BAD_TEXTURE = 3,        /* resolution not 2^n with 0 <= n <= 15, etc.    */
+    HTEX_ERR_OUT_OF_MEMORY = 4,      /* host or device allocation refused             */
+    HTEX_ERR_CUDA = 5,               /* a CUDA runtime call failed                    */
+    HTEX_ERR_QUERY_OUT_OF_RANGE = 6, /* reserved: per-query errors use the status word */
+    HTEX_ERR_TIMEOUT = 7,            /* a bounded host wait ran out                   */
+    HTEX_ERR_UNSUPPORTED = 8         /* valid request this build cannot serve         */
+} htex_status;
+
+/* Texel storage formats.  Every format is filtered in FP32.
+ *   HTEX_F32   IEEE binary32 per channel.
+ *   HTEX_U8    8-bit UNORM per channel: byte b stands for b / 255.
+ *   HTEX_F16   IEEE binary16 code c stands for c * scale_e.
+ *   HTEX_BF16  bfloat16 code c stands for c * scale_e.
+ *   HTEX_E4M3  OCP FP8 E4M3 (no infinities, saturating at 448) code c
+ *              stands for c * scale_e.
+ * scale_e is one FP32 number per texture: max|T| / 448 for E4M3, max|T|
+ * for F16/BF16 (over every stored level of texture e; 1 when the texture
+ * is all zero).  Codes are T / scale_e rounded to nearest, ties to even. */
+typedef enum { HTEX_F32 = 0, HTEX_U8 = 1, HTEX_F16 = 2, HTEX_BF16 = 3, HTEX_E4M3 = 4 } htex_dtype;
+
+/* Texture preparation flags (htex_textures_prepare / _upload). */
+#define HTEX_BUILD_MIPS      1u  /* build every coarser level from level 0 by 2x2 box means   */
+#define HTEX_MIRROR_BOUNDARY 2u  /* fill the unused half of boundary textures (Section 4.3)  */
+#define HTEX_FIX_CORNERS     4u  /* corner pre-processing (Section 4.4)                      */
+#define HTEX_LEVELS_GIVEN    8u  /* the caller supplies every level, not only level 0        */
+
+/* Lookup flags (htex_lookup / _backward). */
+#define HTEX_LOOKUP_BIN      1u  /* reorder queries by halfedge before filtering (scratch)    */
+#define HTEX_LOOKUP_GLOBAL   2u  /* never stage textures in shared memory                     */
+
+/* One query: 16 bytes, 16-byte aligned in device memory.
+ *   h          halfedge id, 0 <= h < H
+ *   u, v       barycentrics on the intrinsic triangle of h (Section 4.2):
+ *              u weighs Vert(h), v weighs Vert(Next(h)), 1 - u - v the
+ *              face centroid.  Finite values off the closed triangle are
+ *              clamped onto it (negatives to 0, then scaled onto u + v = 1).
+ *   footprint  isotropic filter width in quad-uv units: level selection
+ *              lambda = log2(footprint * N_e) per fetched texture; level 0
+ *              when lambda is not > 0 (footprint <= 0 or NaN included), the
+ *              1x1 level when floor(lambda) reaches it, else levels
+ *              floor(lambda) and floor(lambda) + 1 blended linearly. */
+typedef struct {
+    int32_t h;
+    float u, v, footprint;
+} htex_query;
+
+typedef struct CUstream_st* htex_stream;
+
+typedef struct htex_mesh htex_mesh;          /* host-side halfedge mesh (opaque)        */
+typedef struct htex_textures htex_textures;  /* device-resident mesh + textures (opaque) */
+
+/* Human-readable name of a status code (static string). */
+const char* htex_status_string(htex_status s);
+
+/* ---------------------------------------------------------------- meshes */
+
+/* Build the halfedge mesh of a polygon mesh (Section 2, Fig. 2; Section 3).
+ *   face_sizes  host [num_faces], each >= 3
+ *   face_verts  host [sum(face_sizes)], vertex ids in [0, num_verts), each
+ *               face's vertices in order (consistent orientation)
+ * The halfedges of face f are contiguous in the face's vertex order:
+ * Next/Prev cycle within the face, Vert(h) is the origin vertex of h,
+ * Face(h) = f.  Twin(h) is the halfedge running the other way, -1 on the
+ * boundary.  Edge ids: scanning h = 0..H-1, a new id whenever Twin(h) < 0
+ * or h < Twin(h), shared with the twin; so E = (H + boundary halfedges)/2.
+ * Host-only (no GPU needed).  Errors: HTEX_ERR_INVALID_ARG (face smaller
+ * than 3, vertex id out of range, an edge from a vertex to itself),
+ * HTEX_ERR_NONMANIFOLD (a directed edge used by two faces). */
+htex_status htex_mesh_create(const int32_t* face_sizes, int32_t num_faces,
+                             const int32_t* face_verts, int32_t num_verts, htex_mesh** out);
+
+/* Adopt explicit halfedge arrays (host, each [H]), e.g. the Fig. 2 table.
+ * Validated: Next/Prev mutually inverse with cycles of length >= 3, Twin an
+ * involution without fixed points running the opposite way
+ * (Vert(Twin h) = Vert(Next h)), Face constant along Next cycles, Edge a
+ * twin-consistent bijection of halfedge pairs (and boundary halfedges)
+ * onto [0, E).  Host-only.  Errors: HTEX_ERR_INVALID_ARG,
+ * HTEX_ERR_NONMANIFOLD. */
+htex_status htex_mesh_create_from_halfedges(const int32_t* twin, const int32_t* next,
+                                            const int32_t* prev, const int32_t* vert,
+                                            const int32_t* edge, const int32_t* face, int32_t H,
+                                            int32_t num_verts, int32_t num_faces,
+                                            htex_mesh** out);
+
+/* Sizes of a mesh; each output pointer is nullable. */
+htex_status htex_mesh_info(const htex_mesh* m, int32_t* H, int32_t* E, int32_t* num_boundary,
+                           int32_t* num_verts, int32_t* num_faces);
+
+/* Copy the six halfedge operators to host arrays of H int32 (each nullable). */
+htex_status htex_mesh_get_halfedges(const htex_mesh* m, int32_t* twin, int32_t* next,
+                                    int32_t* prev, int32_t* vert, int32_t* edge, int32_t* face);
+
+void htex_mesh_destroy(htex_mesh* m);
+
+/* -------------------------------------------------------------- textures */
+
+/* Pool layout (Section 4.3: one square texture per edge, each sized
+ * independently).  Texture e has resolution N_e = 2^log2_res[e] and
+ * log2_res[e] + 1 levels N_e, N_e/2, ..., 1.  In the pool, texture e starts
+ * at byte offset texture_offsets[e] (textures in edge order, each padded to
+ * a multiple of 16 bytes); its levels follow one another; level l is
+ * row-major [N_l][N_l][channels] of the element type, texel (i, j) being
+ * column i along quad x and row j along quad y, at element
+ * (j * N_l + i) * channels.  Texel centres sit at ((i+1/2)/N_l, (j+1/2)/N_l).
+ * Element sizes: F32 4, U8 1, F16/BF16 2, E4M3 1 bytes.
+ *   log2_res         host [E], each in [0, 15]
+ *   pool_bytes       out: total bytes
+ *   texture_offsets  out, nullable: host [E + 1] byte offsets
+ * Host-only. */
+htex_status htex_textures_layout(const htex_mesh* m, int32_t channels, htex_dtype dtype,
+                                 const int32_t* log2_res, int64_t* pool_bytes,
+                                 int64_t* texture_offsets);
+
+/* Prepare the stored pool on the host, without a GPU.
+ *   texels  host; for HTEX_F32/F16/BF16/E4M3 float32 values, for HTEX_U8
+ *           bytes; per edge in edge order, each row-major [N][N][channels];
+ *           level 0 only, or every level (HTEX_LEVELS_GIVEN) in pool order.
+ *   flags   HTEX_BUILD_MIPS (required unless HTEX_LEVELS_GIVEN),
+ *           HTEX_MIRROR_BOUNDARY, HTEX_FIX_CORNERS, HTEX_LEVELS_GIVEN.
+ * Steps, in this order: with BUILD_MIPS and MIRROR_BOUNDARY level 0 of every
+ * boundary texture is mirrored first; mips: level l+1 texel (i, j) =
+ * ((a + b) + c) + d over the 2x2 block (2i, 2j), (2i+1, 2j), (2i, 2j+1),
+ * (2i+1, 2j+1), times 1/4, evaluated in double and rounded once to float
+ * (U8: (a + b + c + d + 2) >> 2); MIRROR_BOUNDARY: every level of a boundary
+ * texture takes, at texel (i, j) with i + j > N - 1, the value of
+ * (N-1-j, N-1-i) (reflection across the quad diagonal, where the virtual
+ * twin lies, Section 3.2); FIX_CORNERS: for every resolution R, the corner
+ * texels meeting at one mesh vertex or face centroid take their group's
+ * mean (double, rounded to float; U8: round half up), groups joined where
+ * one texel is several corners (R = 1); quantisation to F16/BF16/E4M3 with
+ * the per-texture scale (see htex_dtype).
+ *   pool_out    host [pool_bytes] (see htex_textures_layout)
+ *   scales_out  host [E] float, nullable (1 for F32 and U8)
+ * Errors: HTEX_ERR_INVALID_ARG, HTEX_ERR_BAD_TEXTURE, HTEX_ERR_OUT_OF_MEMORY. */
+htex_status htex_textures_prepare(const htex_mesh* m, int32_t channels, htex_dtype dtype,
+                                  const int32_t* log2_res, const void* texels, uint32_t flags,
+                                  void* pool_out, float* scales_out);
+
+/* Prepare (as htex_textures_prepare) and make the mesh and its textures
+ * resident on the current device.  Allocates device memory owned by the
+ * returned object; copies on 'stream' and synchronises it before
+ * returning.  Refuses with HTEX_ERR_OUT_OF_MEMORY, before allocating,
+ * when the device does not have room. */
+htex_status htex_textures_upload(const htex_mesh* m, int32_t channels, htex_dtype dtype,
+                                 const int32_t* log2_res, const void* texels, uint32_t flags,
+                                 htex_stream stream, htex_textures** out);
+
+/* Same as htex_textures_upload with HTEX_LEVELS_GIVEN: 'texels' holds every
+ * level of every texture (pool order, no padding). */
+htex_status htex_textures_upload_levels(const htex_mesh* m, int32_t channels, htex_dtype dtype,
+                                        const int32_t* log2_res, const void* texels,
+                                        uint32_t flags, htex_stream stream, htex_textures** out);
+
+/* Make an already prepared pool resident (bytes as htex_textures_prepare
+ * writes them; scales [E] nullable for F32/U8).  Synchronises 'stream'. */
+htex_status htex_textures_upload_pool(const htex_mesh* m, int32_t channels, htex_dtype dtype,
+                                      const int32_t* log2_res, const void* pool,
+                                      const float* scales, htex_stream stream,
+                                      htex_textures** out);
+
+/* Sizes of resident textures; each output pointer is nullable.
+ * device_bytes counts every device allocation the object holds. */
+htex_status htex_textures_info(const htex_textures* t, int32_t* channels, htex_dtype* dtype,
+                               int32_t* H, int32_t* E, int64_t* pool_bytes,
+                               int64_t* device_bytes);
+
+/* Copy the resident pool (and scales, nullable) back to the host;
+ * synchronises 'stream'. */
+htex_status htex_textures_download_pool(const htex_textures* t, void* pool, float* scales,
+                                        htex_stream stream);
+
+void htex_textures_destroy(htex_textures* t);
+
+/* ---------------------------------------------------------------- lookups */
+
+/* Filtered lookups (Section 4.4, Alg. 3 with Alg. 2), n queries.
+ *   q         device [n] htex_query (16-byte aligned)
+ *   out       device [n][channels] float (16-byte aligned when channels = 4)
+ *   flags     HTEX_LOOKUP_BIN: counting-sort the queries by halfedge first
+ *             (needs scratch: allocated stream-ordered on 'stream' and
+ *             released there); HTEX_LOOKUP_GLOBAL: never stage the pool in
+ *             shared memory (by default a pool of at most 96 KiB is staged)
+ *   d_status  device int32, nullable: incremented once per invalid query
+ * For each query: own = quad of Edge(h) at Alg. 2 (h, (u, v)), then the
+ * quads of Next(h) at (v, -u) and of Prev(h) at (-v, u); each fetch is a
+ * bilinear (or trilinear, see htex_query) sample with zero border whose
+ * in-bounds weights form the normalisation sum (the border-normalisation
+ * channel of Section 4.4, computed instead of stored); the result is the
+ * data sum over the three fetches divided by the weight sum.  Accumulates
+ * in FP32.  n = 0 is valid and launches nothing.  Asynchronous. */
+htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,
+                        uint32_t flags, htex_stream stream, int32_t* d_status);
+
+/* Gradient of L = sum_q sum_c grad_out[q][c] * lookup(q)[c] with respect to
+ * every stored texel value (the decoded value T = code * scale for scaled
+ * formats).  The lookup is linear in the texels, so each in-bounds tap k
+ * of query q receives grad_out[q][c] * w_k / W_q with the forward weights.
+ *   grad_out     device [n][channels] float
+ *   grad_texels  device float, one per pool element (pool_bytes / element
+ *                size), same element order as the pool; accumulated into
+ *                (the caller zeroes it); padding elements stay untouched
+ *   d_status     as for htex_lookup
+ * Uses float atomics: the summation order, hence the last bits, may vary
+ * from run to run.  Asynchronous. */
+htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, int64_t n,
+                                 const float* grad_out, float* grad_texels, uint32_t flags,
+                                 htex_stream stream, int32_t* d_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTEX_H */

@@ -1,0 +1,268 @@
+"""Htex batched seamless filtered lookups on GB300 (sm_103a).
+
+Python face of libhtex (C ABI in include/htex.h): argument marshalling
+only, every step of the lookup runs in the library's CUDA kernels.
+PyTorch supplies device memory and streams.
+
+    mesh = Mesh(face_sizes, face_verts, num_verts)          # Section 2, Fig. 2
+    tex = Textures.upload(mesh, log2_res, texels, channels=4, dtype="u8")
+    out = lookup(tex, queries)          # queries: int32 [n, 4] (h, u, v, footprint bits)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import (BUILD_MIPS, DTYPES, ELEM_SIZE, FIX_CORNERS, LEVELS_GIVEN, LOOKUP_BIN,
+                   LOOKUP_GLOBAL, MIRROR_BOUNDARY, HtexError, check, load)
+
+__all__ = ["Mesh", "Textures", "lookup", "lookup_backward", "pack_queries", "HtexLookup",
+           "HtexError", "BUILD_MIPS", "MIRROR_BOUNDARY", "FIX_CORNERS", "LEVELS_GIVEN",
+           "LOOKUP_BIN", "LOOKUP_GLOBAL"]
+
+
+def _np(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Mesh:
+    """Host-side halfedge mesh (htex_mesh_create / _create_from_halfedges)."""
+
+    def __init__(self, face_sizes=None, face_verts=None, num_verts: int = 0, *, _handle=None):
+        self._lib = load()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            fs, fv = _np(face_sizes, np.int32), _np(face_verts, np.int32)
+            h = ctypes.c_void_p()
+            check(self._lib.htex_mesh_create(_ptr(fs), int(fs.shape[0]), _ptr(fv), int(num_verts),
+                                             ctypes.byref(h)), "htex_mesh_create")
+            self._h = h
+        vals = [ctypes.c_int32() for _ in range(5)]
+        check(self._lib.htex_mesh_info(self._h, *[ctypes.byref(v) for v in vals]), "htex_mesh_info")
+        self.H, self.E, self.num_boundary, self.num_verts, self.num_faces = [v.value for v in vals]
+
+    @classmethod
+    def from_halfedges(cls, twin, next, prev, vert, edge, face, num_verts: int, num_faces: int):
+        lib = load()
+        arrs = [_np(a, np.int32) for a in (twin, next, prev, vert, edge, face)]
+        h = ctypes.c_void_p()
+        check(lib.htex_mesh_create_from_halfedges(*[_ptr(a) for a in arrs], int(arrs[0].shape[0]),
+                                                  int(num_verts), int(num_faces), ctypes.byref(h)),
+              "htex_mesh_create_from_halfedges")
+        return cls(_handle=h)
+
+    def halfedges(self) -> dict:
+        arrs = {k: np.empty(self.H, np.int32) for k in ("twin", "next", "prev", "vert", "edge", "face")}
+        check(self._lib.htex_mesh_get_halfedges(self._h, *[_ptr(a) for a in arrs.values()]),
+              "htex_mesh_get_halfedges")
+        return arrs
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.htex_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def _texel_array(texels, dtype: str) -> np.ndarray:
+    return _np(texels, np.uint8 if dtype == "u8" else np.float32).reshape(-1)
+
+
+class Textures:
+    """Device-resident mesh + textures (htex_textures_*)."""
+
+    def __init__(self, handle, mesh: Mesh):
+        self._lib = load()
+        self._h = handle
+        ch, dt, H, E = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        pb, db = ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.htex_textures_info(handle, ctypes.byref(ch), ctypes.byref(dt), ctypes.byref(H),
+                                           ctypes.byref(E), ctypes.byref(pb), ctypes.byref(db)),
+              "htex_textures_info")
+        self.channels, self.H, self.E = ch.value, H.value, E.value
+        self.dtype = {v: k for k, v in DTYPES.items()}[dt.value]
+        self.pool_bytes, self.device_bytes = pb.value, db.value
+        self.mesh = mesh
+
+    @staticmethod
+    def layout(mesh: Mesh, log2_res, channels: int, dtype: str):
+        lib = load()
+        ln = _np(log2_res, np.int32)
+        total = ctypes.c_int64()
+        offs = np.empty(mesh.E + 1, np.int64)
+        check(lib.htex_textures_layout(mesh._h, int(channels), DTYPES[dtype], _ptr(ln), ctypes.byref(total),
+                                       _ptr(offs)), "htex_textures_layout")
+        return int(total.value), offs
+
+    @staticmethod
+    def prepare(mesh: Mesh, log2_res, texels, channels: int, dtype: str = "f32", flags: int = BUILD_MIPS):
+        """Host-side preparation: the stored pool bytes and per-texture scales."""
+        lib = load()
+        ln = _np(log2_res, np.int32)
+        total, _ = Textures.layout(mesh, ln, channels, dtype)
+        pool = np.empty(max(total, 1), np.uint8)
+        scales = np.empty(max(mesh.E, 1), np.float32)
+        tx = _texel_array(texels, dtype)
+        check(lib.htex_textures_prepare(mesh._h, int(channels), DTYPES[dtype], _ptr(ln), _ptr(tx), int(flags),
+                                        _ptr(pool), _ptr(scales)), "htex_textures_prepare")
+        return pool[:total], scales[:mesh.E]
+
+    @classmethod
+    def upload(cls, mesh: Mesh, log2_res, texels, channels: int, dtype: str = "f32",
+               flags: int = BUILD_MIPS, stream=None):
+        lib = load()
+        ln = _np(log2_res, np.int32)
+        tx = _texel_array(texels, dtype)
+        h = ctypes.c_void_p()
+        check(lib.htex_textures_upload(mesh._h, int(channels), DTYPES[dtype], _ptr(ln), _ptr(tx), int(flags),
+                                       _stream(stream), ctypes.byref(h)), "htex_textures_upload")
+        return cls(h, mesh)
+
+    @classmethod
+    def upload_levels(cls, mesh: Mesh, log2_res, texels, channels: int, dtype: str = "f32",
+                      flags: int = 0, stream=None):
+        lib = load()
+        ln = _np(log2_res, np.int32)
+        tx = _texel_array(texels, dtype)
+        h = ctypes.c_void_p()
+        check(lib.htex_textures_upload_levels(mesh._h, int(channels), DTYPES[dtype], _ptr(ln), _ptr(tx),
+                                              int(flags), _stream(stream), ctypes.byref(h)),
+              "htex_textures_upload_levels")
+        return cls(h, mesh)
+
+    @classmethod
+    def upload_pool(cls, mesh: Mesh, log2_res, pool, scales, channels: int, dtype: str, stream=None):
+        lib = load()
+        ln = _np(log2_res, np.int32)
+        pool = _np(pool, np.uint8)
+        sc = _np(scales, np.float32) if scales is not None else None
+        h = ctypes.c_void_p()
+        check(lib.htex_textures_upload_pool(mesh._h, int(channels), DTYPES[dtype], _ptr(ln), _ptr(pool),
+                                            _ptr(sc) if sc is not None else None, _stream(stream),
+                                            ctypes.byref(h)), "htex_textures_upload_pool")
+        return cls(h, mesh)
+
+    def download_pool(self, stream=None):
+        pool = np.empty(max(self.pool_bytes, 1), np.uint8)
+        scales = np.empty(max(self.E, 1), np.float32)
+        check(self._lib.htex_textures_download_pool(self._h, _ptr(pool), _ptr(scales), _stream(stream)),
+              "htex_textures_download_pool")
+        return pool[:self.pool_bytes], scales[:self.E]
+
+    @property
+    def pool_elements(self) -> int:
+        return self.pool_bytes // ELEM_SIZE[self.dtype]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.htex_textures_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def pack_queries(h, u, v, footprint=None):
+    """AoS queries as an int32 numpy array [n, 4]: h, then the float32 bits of u, v, footprint."""
+    h = _np(h, np.int32)
+    n = h.shape[0]
+    q = np.empty((n, 4), np.int32)
+    q[:, 0] = h
+    q[:, 1] = _np(u, np.float32).view(np.int32)
+    q[:, 2] = _np(v, np.float32).view(np.int32)
+    f = np.zeros(n, np.float32) if footprint is None else _np(footprint, np.float32)
+    q[:, 3] = f.view(np.int32)
+    return q
+
+
+def _check_tensor(t, name, dtype, cols):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous() or t.dim() != 2 or t.shape[1] != cols:
+        raise ValueError(f"{name} must be contiguous {dtype} [n, {cols}]")
+
+
+def lookup(tex: Textures, queries, out=None, flags: int = 0, stream=None, status=None):
+    """htex_lookup: queries int32 CUDA tensor [n, 4] -> float32 [n, channels]."""
+    import torch
+    _check_tensor(queries, "queries", torch.int32, 4)
+    n = queries.shape[0]
+    if out is None:
+        out = torch.empty((n, tex.channels), dtype=torch.float32, device=queries.device)
+    else:
+        _check_tensor(out, "out", torch.float32, tex.channels)
+    st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    check(tex._lib.htex_lookup(tex._h, ctypes.c_void_p(queries.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
+                               int(flags), _stream(stream), st), "htex_lookup")
+    return out
+
+
+def lookup_backward(tex: Textures, queries, grad_out, grad_texels=None, flags: int = 0, stream=None,
+                    status=None):
+    """htex_lookup_backward: accumulates into a pool-shaped float32 gradient and returns it."""
+    import torch
+    _check_tensor(queries, "queries", torch.int32, 4)
+    _check_tensor(grad_out, "grad_out", torch.float32, tex.channels)
+    if grad_texels is None:
+        grad_texels = torch.zeros(tex.pool_elements, dtype=torch.float32, device=queries.device)
+    st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    check(tex._lib.htex_lookup_backward(tex._h, ctypes.c_void_p(queries.data_ptr()), queries.shape[0],
+                                        ctypes.c_void_p(grad_out.data_ptr()),
+                                        ctypes.c_void_p(grad_texels.data_ptr()), int(flags), _stream(stream),
+                                        st), "htex_lookup_backward")
+    return grad_texels
+
+
+def _autograd():
+    import torch
+
+    class HtexLookup(torch.autograd.Function):
+        """out = lookup(tex, queries) with d out / d texels through htex_lookup_backward.
+
+        ``texels`` is a pool-shaped float32 tensor that stands for the
+        resident pool (its values live in ``tex``); its gradient is the
+        pool-shaped texel gradient."""
+
+        @staticmethod
+        def forward(ctx, texels, tex, queries):
+            ctx.tex = tex
+            ctx.save_for_backward(queries)
+            return lookup(tex, queries)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (queries,) = ctx.saved_tensors
+            g = lookup_backward(ctx.tex, queries, grad_out.contiguous().float())
+            return g, None, None
+
+    return HtexLookup
+
+
+class _LazyFn:
+    _fn = None
+
+    def apply(self, *a):
+        if _LazyFn._fn is None:
+            _LazyFn._fn = _autograd()
+        return _LazyFn._fn.apply(*a)
+
+
+HtexLookup = _LazyFn()

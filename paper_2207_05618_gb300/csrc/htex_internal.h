@@ -1,0 +1,70 @@
+// Internal declarations of libhtex (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "htex.h"
+
+// Host-side halfedge mesh: the six operators of the paper's halfedge
+// representation (Section 2, Fig. 2), one int32 array each.
+struct htex_mesh {
+    int32_t H = 0, E = 0, B = 0, V = 0, F = 0;
+    std::vector<int32_t> twin, next, prev, vert, edge, face;
+};
+
+// Device-resident asset: packed per-halfedge lookup records, per-edge
+// texture headers, per-edge scales and the texel pool.
+//
+// Lookup record of halfedge h (16 bytes): the three halfedges Alg. 3
+// visits are h, Next(h) and Prev(h); for each, the edge (texture) it maps
+// to through Edge(.) and whether Alg. 2 reflects its coordinates
+// (bit 31 set when g < Twin(g)).  w holds Face(h).
+//
+// Texture header of edge e (16 bytes): x = byte offset / 16, y = log2 N_e,
+// z = scale bits (float), w = 0.
+struct htex_textures {
+    int32_t H = 0, E = 0, C = 0;
+    htex_dtype dtype = HTEX_F32;
+    int32_t uniform_log2n = -1;      // >= 0 when every texture has that resolution
+    int64_t uniform_stride = 0;      // bytes per texture when uniform
+    int64_t pool_bytes = 0;
+    int64_t device_bytes = 0;
+    int32_t max_log2n = 0;
+    bool has_scales = false;
+    void* d_rec = nullptr;           // int4 [H]
+    void* d_hdr = nullptr;           // int4 [E]
+    void* d_scale = nullptr;         // float [E]
+    void* d_pool = nullptr;          // bytes [pool_bytes]
+    int device = 0;
+    int num_sms = 0;
+};
+
+constexpr uint32_t kFlipBit = 0x80000000u;
+constexpr int kMaxLog2Res = 15;
+
+int htex_elem_size(htex_dtype d);
+bool htex_dtype_valid(int32_t d);
+
+// Texels of a full chain 2^n, 2^(n-1), ..., 1.
+inline int64_t htex_chain_texels(int n) {
+    return ((int64_t(1) << (2 * n + 2)) - 1) / 3;
+}
+
+// Texel offset of level l inside a chain of base 2^n.
+inline int64_t htex_level_texels(int n, int l) {
+    return ((int64_t(1) << (2 * n + 2)) - (int64_t(1) << (2 * (n - l) + 2))) / 3;
+}
+
+// Byte offsets of every texture in the pool; returns total bytes.
+int64_t htex_pool_offsets(int32_t E, const int32_t* log2n, int32_t C, htex_dtype dt,
+                          int64_t* offsets /* [E+1], nullable */);
+
+// Kernel launchers (lookup.cu, backward.cu).  They validate nothing: the
+// C-ABI entry points have checked every argument.
+htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int64_t n,
+                               float* out, uint32_t flags, htex_stream stream,
+                               int32_t* d_status);
+htex_status htex_launch_backward(const htex_textures* t, const htex_query* q, int64_t n,
+                                 const float* grad_out, float* grad_texels, uint32_t flags,
+                                 htex_stream stream, int32_t* d_status);

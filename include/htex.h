@@ -42,7 +42,7 @@ typedef enum {
     HTEX_OK = 0,
     HTEX_ERR_INVALID_ARG = 1,        /* null pointer, bad size, bad enum value        */
     HTEX_ERR_NONMANIFOLD = 2,        /* a directed edge used twice, or twins disagree */
-    HTEX_ERR_BAD_TEXTURE = 3,        /* resolution not 2^n with 0 <= n <= 15, etc.    */
+    HTEX_ERR_BAD_TEXTURE = 3,        /* resolution not 2^n with 0 <= n <= 13, etc.    */
     HTEX_ERR_OUT_OF_MEMORY = 4,      /* host or device allocation refused             */
     HTEX_ERR_CUDA = 5,               /* a CUDA runtime call failed                    */
     HTEX_ERR_QUERY_OUT_OF_RANGE = 6, /* reserved: per-query errors use the status word */
@@ -147,7 +147,7 @@ void htex_mesh_destroy(htex_mesh* m);
  * column i along quad x and row j along quad y, at element
  * (j * N_l + i) * channels.  Texel centres sit at ((i+1/2)/N_l, (j+1/2)/N_l).
  * Element sizes: F32 4, U8 1, F16/BF16 2, E4M3 1 bytes.
- *   log2_res         host [E], each in [0, 15]
+ *   log2_res         host [E], each in [0, 13] (up to 8192 x 8192 texels)
  *   pool_bytes       out: total bytes
  *   texture_offsets  out, nullable: host [E + 1] byte offsets
  * Host-only. */

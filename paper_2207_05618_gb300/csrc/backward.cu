@@ -1,11 +1,11 @@
 // Adjoint of the filtered lookup and the htex_lookup_backward entry point.
 //
 // The lookup is linear in the stored texels: out_c = sum_k w_k T_k,c / W
-// with W the sum of the in-bounds weights of all taps of the three fetches.
-// So dL/dT_k,c = sum over queries of grad_out_c * w_k / W.  Per query the
-// kernel first recomputes W from the coordinates alone (no texel loads),
-// then scatter-adds grad_out * w_k / W into every in-bounds tap with
-// nonzero weight: float4/float2 atomics where a texel's channels are
+// with W the sum of the in-bounds weights of all taps of the three fetches
+// (Alg. 3).  So dL/dT_k,c = sum over queries of grad_out_c * w_k / W.  Per
+// query the kernel first recomputes W from the coordinates alone (no texel
+// loads), then scatter-adds grad_out * w_k / W into every in-bounds tap
+// with nonzero weight: float4/float2 atomics where a texel's channels are
 // contiguous and aligned, scalar atomics otherwise.
 #include <cuda_runtime.h>
 
@@ -21,22 +21,20 @@ struct BwdParams {
     int32_t* status;
 };
 
-template <int DT, class S>
-__device__ __forceinline__ float level_weight(const TexRef& t, int l, float x, float y) {
-    Taps k;
-    if (!taps(x, y, 1 << (t.n - l), k)) return 0.0f;
-    return (k.wx0 + k.wx1) * (k.wy0 + k.wy1);
+// The forward weights, recomputed: each fetch decomposed as in the forward
+// kernel (own 2x2 block, Next/Prev one texel row or column per level).
+__device__ __forceinline__ float own_weight(int n, int l, float x, float y) {
+    const int N = 1 << (n - l);
+    const Taps1 tx = taps1(x, N), ty = taps1(y, N);
+    return (tx.w0 + tx.w1) * (ty.w0 + ty.w1);
 }
 
-template <int DT, class S>
-__device__ __forceinline__ float fetch_weight(const Asset<S>& A, uint32_t code, float a, float b, float lf) {
-    float x, y;
-    quad_coords(code, a, b, x, y);
-    const TexRef t = tex_ref<DT>(A, code & ~kFlipBit);
-    const Lod d = select_lod(lf, t.n);
-    float w = d.w0 * level_weight<DT, S>(t, d.l0, x, y);
-    if (d.l1 >= 0) w = fmaf(d.w1, level_weight<DT, S>(t, d.l1, x, y), w);
-    return w;
+__device__ __forceinline__ float edge_weight(int n, int l, float dist, float along, bool flip) {
+    const int N = 1 << (n - l);
+    const float wa = across_weight(dist, N);
+    if (!(wa > 0.0f)) return 0.0f;
+    const Taps1 ta = taps1(flip ? 1.0f - along : along, N);
+    return wa * (ta.w0 + ta.w1);
 }
 
 template <int C>
@@ -53,27 +51,52 @@ __device__ __forceinline__ void add_texel(float* grad, uint64_t elem, float w, c
 }
 
 template <int DT, int C>
-__device__ __forceinline__ void scatter_level(float* grad, const TexRef& t, int l, float x, float y, float wl,
-                                              const float (&g)[C]) {
-    Taps k;
-    if (!taps(x, y, 1 << (t.n - l), k)) return;
+__device__ __forceinline__ void own_scatter(float* grad, const TexRef& t, int l, float x, float y, float wl,
+                                            const float (&g)[C]) {
     constexpr int ES = Fmt<DT>::ES;
-    const uint64_t lvl = (t.off + level_bytes(t.n, l, C * ES)) / ES;   // element index
-    add_texel<C>(grad, lvl + uint64_t(k.j0 * k.N + k.i0) * C, wl * k.wy0 * k.wx0, g);
-    add_texel<C>(grad, lvl + uint64_t(k.j0 * k.N + k.i1) * C, wl * k.wy0 * k.wx1, g);
-    add_texel<C>(grad, lvl + uint64_t(k.j1 * k.N + k.i0) * C, wl * k.wy1 * k.wx0, g);
-    add_texel<C>(grad, lvl + uint64_t(k.j1 * k.N + k.i1) * C, wl * k.wy1 * k.wx1, g);
+    const int N = 1 << (t.n - l);
+    const Taps1 tx = taps1(x, N), ty = taps1(y, N);
+    const uint64_t lvl = t.off / ES + uint64_t(level_texels(t.n, l)) * C;   // element index
+    add_texel<C>(grad, lvl + uint64_t(ty.i0 * N + tx.i0) * C, wl * ty.w0 * tx.w0, g);
+    add_texel<C>(grad, lvl + uint64_t(ty.i0 * N + tx.i1) * C, wl * ty.w0 * tx.w1, g);
+    add_texel<C>(grad, lvl + uint64_t(ty.i1 * N + tx.i0) * C, wl * ty.w1 * tx.w0, g);
+    add_texel<C>(grad, lvl + uint64_t(ty.i1 * N + tx.i1) * C, wl * ty.w1 * tx.w1, g);
 }
 
-template <int DT, int C, class S>
-__device__ __forceinline__ void scatter_fetch(const Asset<S>& A, float* grad, uint32_t code, float a, float b,
-                                              float lf, const float (&g)[C]) {
-    float x, y;
-    quad_coords(code, a, b, x, y);
-    const TexRef t = tex_ref<DT>(A, code & ~kFlipBit);
-    const Lod d = select_lod(lf, t.n);
-    scatter_level<DT, C>(grad, t, d.l0, x, y, d.w0, g);
-    if (d.l1 >= 0) scatter_level<DT, C>(grad, t, d.l1, x, y, d.w1, g);
+template <int DT, int C, bool ROW>
+__device__ __forceinline__ void edge_scatter(float* grad, const TexRef& t, int l, float dist, float along, bool flip,
+                                             float wl, const float (&g)[C]) {
+    constexpr int ES = Fmt<DT>::ES;
+    const int N = 1 << (t.n - l);
+    const float wa = across_weight(dist, N);
+    if (!(wa > 0.0f)) return;
+    const Taps1 ta = taps1(flip ? 1.0f - along : along, N);
+    const int k = flip ? N - 1 : 0;
+    const uint64_t lvl = t.off / ES + uint64_t(level_texels(t.n, l)) * C;
+    const uint64_t e0 = ROW ? uint64_t(k * N + ta.i0) : uint64_t(ta.i0 * N + k);
+    const uint64_t e1 = ROW ? uint64_t(k * N + ta.i1) : uint64_t(ta.i1 * N + k);
+    add_texel<C>(grad, lvl + e0 * C, wl * wa * ta.w0, g);
+    add_texel<C>(grad, lvl + e1 * C, wl * wa * ta.w1, g);
+}
+
+// One query's three fetches: their textures, level choices and coordinates.
+struct Fetches {
+    TexRef t[3];
+    Lod d[3];
+    bool flip[3];
+};
+
+template <int DT, class S>
+__device__ __forceinline__ Fetches plan(const Asset<S>& A, uint4 rec, float lf) {
+    Fetches F;
+    const uint32_t code[3] = {rec.x, rec.y, rec.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        F.t[k] = tex_ref<DT>(A, code[k] & ~kFlipBit);
+        F.d[k] = select_lod(lf, F.t[k].n);
+        F.flip[k] = code[k] & kFlipBit;
+    }
+    return F;
 }
 
 template <int DT, int C>
@@ -87,16 +110,25 @@ __global__ void __launch_bounds__(256) k_backward(Asset<GlobalSpace> A, BwdParam
             continue;
         }
         const uint4 rec = A.rec.ld16(uint64_t(h) * 16u);
-        const float lf = footprint_log2(f);
-        const float W = fetch_weight<DT>(A, rec.x, u, v, lf) + fetch_weight<DT>(A, rec.y, v, -u, lf) +
-                        fetch_weight<DT>(A, rec.z, -v, u, lf);
-        const float inv = 1.0f / W;
+        const Fetches F = plan<DT>(A, rec, footprint_log2(f));
+        const float x = F.flip[0] ? 1.0f - u : u, y = F.flip[0] ? 1.0f - v : v;
+        float W = 0.0f;
+        W = fmaf(F.d[0].w0, own_weight(F.t[0].n, F.d[0].l0, x, y), W);
+        if (F.d[0].l1 >= 0) W = fmaf(F.d[0].w1, own_weight(F.t[0].n, F.d[0].l1, x, y), W);
+        W = fmaf(F.d[1].w0, edge_weight(F.t[1].n, F.d[1].l0, u, v, F.flip[1]), W);
+        if (F.d[1].l1 >= 0) W = fmaf(F.d[1].w1, edge_weight(F.t[1].n, F.d[1].l1, u, v, F.flip[1]), W);
+        W = fmaf(F.d[2].w0, edge_weight(F.t[2].n, F.d[2].l0, v, u, F.flip[2]), W);
+        if (F.d[2].l1 >= 0) W = fmaf(F.d[2].w1, edge_weight(F.t[2].n, F.d[2].l1, v, u, F.flip[2]), W);
+        const float inv = __frcp_rn(W);
         float g[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) g[c] = __ldcs(p.gout + i * C + c) * inv;
-        scatter_fetch<DT, C>(A, p.grad, rec.x, u, v, lf, g);
-        scatter_fetch<DT, C>(A, p.grad, rec.y, v, -u, lf, g);
-        scatter_fetch<DT, C>(A, p.grad, rec.z, -v, u, lf, g);
+        own_scatter<DT, C>(p.grad, F.t[0], F.d[0].l0, x, y, F.d[0].w0, g);
+        if (F.d[0].l1 >= 0) own_scatter<DT, C>(p.grad, F.t[0], F.d[0].l1, x, y, F.d[0].w1, g);
+        edge_scatter<DT, C, true>(p.grad, F.t[1], F.d[1].l0, u, v, F.flip[1], F.d[1].w0, g);
+        if (F.d[1].l1 >= 0) edge_scatter<DT, C, true>(p.grad, F.t[1], F.d[1].l1, u, v, F.flip[1], F.d[1].w1, g);
+        edge_scatter<DT, C, false>(p.grad, F.t[2], F.d[2].l0, v, u, F.flip[2], F.d[2].w0, g);
+        if (F.d[2].l1 >= 0) edge_scatter<DT, C, false>(p.grad, F.t[2], F.d[2].l1, v, u, F.flip[2], F.d[2].w1, g);
     }
 }
 

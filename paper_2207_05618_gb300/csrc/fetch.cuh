@@ -24,6 +24,37 @@ struct GlobalSpace {
     __device__ __forceinline__ uint32_t ld4(off_t o) const { return __ldg(reinterpret_cast<const unsigned int*>(base + o)); }
     __device__ __forceinline__ uint32_t ld2(off_t o) const { return __ldg(reinterpret_cast<const unsigned short*>(base + o)); }
     __device__ __forceinline__ uint32_t ld1(off_t o) const { return __ldg(reinterpret_cast<const unsigned char*>(base + o)); }
+    // Predicated loads: no memory access and a zero result when p is false.
+    __device__ __forceinline__ uint4 ld16_if(bool p, off_t o) const {
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+            : "+r"(r.x), "+r"(r.y), "+r"(r.z), "+r"(r.w) : "l"(base + o), "r"(uint32_t(p)));
+        return r;
+    }
+    __device__ __forceinline__ uint2 ld8_if(bool p, off_t o) const {
+        uint2 r = make_uint2(0u, 0u);
+        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q ld.global.nc.v2.u32 {%0, %1}, [%2];\n\t}"
+            : "+r"(r.x), "+r"(r.y) : "l"(base + o), "r"(uint32_t(p)));
+        return r;
+    }
+    __device__ __forceinline__ uint32_t ld4_if(bool p, off_t o) const {
+        uint32_t r = 0u;
+        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u32 %0, [%1];\n\t}"
+            : "+r"(r) : "l"(base + o), "r"(uint32_t(p)));
+        return r;
+    }
+    __device__ __forceinline__ uint32_t ld2_if(bool p, off_t o) const {
+        unsigned short r = 0;
+        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u16 %0, [%1];\n\t}"
+            : "+h"(r) : "l"(base + o), "r"(uint32_t(p)));
+        return r;
+    }
+    __device__ __forceinline__ uint32_t ld1_if(bool p, off_t o) const {
+        unsigned short r = 0;
+        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u8 %0, [%1];\n\t}"
+            : "+h"(r) : "l"(base + o), "r"(uint32_t(p)));
+        return r & 0xffu;
+    }
 };
 
 // Shared memory addressed by 32-bit shared-window addresses.
@@ -53,6 +84,36 @@ struct SharedSpace {
     __device__ __forceinline__ uint32_t ld1(off_t o) const {
         unsigned short r;
         asm volatile("ld.shared.u8 %0, [%1];" : "=h"(r) : "r"(base + o));
+        return r & 0xffu;
+    }
+    __device__ __forceinline__ uint4 ld16_if(bool p, off_t o) const {
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+                     : "+r"(r.x), "+r"(r.y), "+r"(r.z), "+r"(r.w) : "r"(base + o), "r"(uint32_t(p)));
+        return r;
+    }
+    __device__ __forceinline__ uint2 ld8_if(bool p, off_t o) const {
+        uint2 r = make_uint2(0u, 0u);
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q ld.shared.v2.u32 {%0, %1}, [%2];\n\t}"
+                     : "+r"(r.x), "+r"(r.y) : "r"(base + o), "r"(uint32_t(p)));
+        return r;
+    }
+    __device__ __forceinline__ uint32_t ld4_if(bool p, off_t o) const {
+        uint32_t r = 0u;
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.u32 %0, [%1];\n\t}"
+                     : "+r"(r) : "r"(base + o), "r"(uint32_t(p)));
+        return r;
+    }
+    __device__ __forceinline__ uint32_t ld2_if(bool p, off_t o) const {
+        unsigned short r = 0;
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.u16 %0, [%1];\n\t}"
+                     : "+h"(r) : "r"(base + o), "r"(uint32_t(p)));
+        return r;
+    }
+    __device__ __forceinline__ uint32_t ld1_if(bool p, off_t o) const {
+        unsigned short r = 0;
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.u8 %0, [%1];\n\t}"
+                     : "+h"(r) : "r"(base + o), "r"(uint32_t(p)));
         return r & 0xffu;
     }
 };
@@ -135,6 +196,106 @@ __device__ __forceinline__ void load_texel(const S& s, typename S::off_t o, floa
     }
 }
 
+// One texel, loaded only when p (else all channels zero).
+template <int DT, int C, class S>
+__device__ __forceinline__ void load_texel_if(const S& s, bool p, typename S::off_t o, float (&t)[C]) {
+    constexpr int ES = Fmt<DT>::ES;
+    if constexpr (DT == HTEX_F32) {
+        if constexpr (C == 4) {
+            const uint4 r = s.ld16_if(p, o);
+            t[0] = __uint_as_float(r.x); t[1] = __uint_as_float(r.y);
+            t[2] = __uint_as_float(r.z); t[3] = __uint_as_float(r.w);
+        } else if constexpr (C == 2) {
+            const uint2 r = s.ld8_if(p, o);
+            t[0] = __uint_as_float(r.x); t[1] = __uint_as_float(r.y);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) t[c] = __uint_as_float(s.ld4_if(p, o + 4 * c));
+        }
+    } else if constexpr (ES == 1) {
+        if constexpr (C == 4) {
+            const uint32_t r = s.ld4_if(p, o);
+            if constexpr (DT == HTEX_E4M3) {
+                const float2 lo = dec_e4m3x2(r & 0xffffu), hi = dec_e4m3x2(r >> 16);
+                t[0] = lo.x; t[1] = lo.y; t[2] = hi.x; t[3] = hi.y;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) t[c] = dec1<DT>((r >> (8 * c)) & 0xffu);
+            }
+        } else if constexpr (C == 2) {
+            const uint32_t r = s.ld2_if(p, o);
+            t[0] = dec1<DT>(r & 0xffu); t[1] = dec1<DT>(r >> 8);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) t[c] = dec1<DT>(s.ld1_if(p, o + c));
+        }
+    } else {
+        if constexpr (C == 4) {
+            const uint2 r = s.ld8_if(p, o);
+            t[0] = dec1<DT>(r.x & 0xffffu); t[1] = dec1<DT>(r.x >> 16);
+            t[2] = dec1<DT>(r.y & 0xffffu); t[3] = dec1<DT>(r.y >> 16);
+        } else if constexpr (C == 2) {
+            const uint32_t r = s.ld4_if(p, o);
+            t[0] = dec1<DT>(r & 0xffffu); t[1] = dec1<DT>(r >> 16);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) t[c] = dec1<DT>(s.ld2_if(p, o + 2 * c));
+        }
+    }
+}
+
+// Raw storage of one texel as loaded (decoded later), for the formats whose
+// texel fits 8 bytes: one or two registers instead of C floats.
+template <int DT, int C>
+struct Raw {
+    static constexpr int TB = C * Fmt<DT>::ES;
+    static constexpr bool PACKED = (TB == 1 || TB == 2 || TB == 4);   // one register per texel
+    uint32_t a = 0u, b = 0u;
+
+    template <class S>
+    __device__ __forceinline__ void load_if(const S& s, bool p, typename S::off_t o) {
+        if constexpr (TB == 8) {
+            const uint2 r = s.ld8_if(p, o);
+            a = r.x;
+            b = r.y;
+        } else if constexpr (TB == 4) {
+            a = s.ld4_if(p, o);
+        } else if constexpr (TB == 2) {
+            a = s.ld2_if(p, o);
+        } else {
+            a = s.ld1_if(p, o);
+        }
+    }
+
+    __device__ __forceinline__ void decode(float (&t)[C]) const {
+        if constexpr (DT == HTEX_F32) {
+            t[0] = __uint_as_float(a);
+            if constexpr (C == 2) t[1] = __uint_as_float(b);
+        } else if constexpr (Fmt<DT>::ES == 1) {
+            if constexpr (DT == HTEX_E4M3 && C >= 2) {
+                const float2 lo = dec_e4m3x2(a & 0xffffu);
+                t[0] = lo.x;
+                t[1] = lo.y;
+                if constexpr (C == 4) {
+                    const float2 hi = dec_e4m3x2(a >> 16);
+                    t[2] = hi.x;
+                    t[3] = hi.y;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) t[c] = dec1<DT>((a >> (8 * c)) & 0xffu);
+            }
+        } else {
+            t[0] = dec1<DT>(a & 0xffffu);
+            if constexpr (C >= 2) t[1] = dec1<DT>(a >> 16);
+            if constexpr (C == 4) {
+                t[2] = dec1<DT>(b & 0xffffu);
+                t[3] = dec1<DT>(b >> 16);
+            }
+        }
+    }
+};
+
 // ---------------------------------------------------------------- asset
 
 // A resident asset seen from one memory space.
@@ -171,10 +332,11 @@ __device__ __forceinline__ TexRef tex_ref(const Asset<S>& A, uint32_t e) {
     return t;
 }
 
-// Byte offset of level l inside a chain of base 2^n with 'tb' bytes per texel.
-__device__ __forceinline__ uint64_t level_bytes(int n, int l, int tb) {
-    const uint64_t t = ((uint64_t(1) << (2 * n + 2)) - (uint64_t(1) << (2 * (n - l) + 2))) / 3u;
-    return t * uint64_t(tb);
+// Texels before level l in a chain of base 2^n: sum_{k<l} 4^(n-k)
+// = 4^(n-l+1) (4^l - 1) / 3, where (4^l - 1) / 3 is the bit pattern 0101..01
+// (l pairs).  Fits 32 bits for n <= 15.
+__device__ __forceinline__ uint32_t level_texels(int n, int l) {
+    return l ? ((0x55555555u & ((1u << (2 * l)) - 1u)) << (2 * (n - l + 1))) : 0u;
 }
 
 // Level choice of one fetch: levels l0 (weight w0) and l1 (weight w1, l1 < 0
@@ -202,31 +364,101 @@ __device__ __forceinline__ Lod select_lod(float log2f_fp, int n) {
     return d;
 }
 
-// Bilinear taps of one level with a zero border: texel centres at
-// (i + 1/2) / N; the 1-D weights of out-of-range taps are zero, so
-// (wx0 + wx1) (wy0 + wy1) is this level's share of the normalisation sum.
-struct Taps {
-    int N;
-    int i0, i1, j0, j1;     // clamped texel indices
-    float wx0, wx1, wy0, wy1;
+// Two taps along one axis at coordinate p in [0, 1] on a level of N
+// texels with a zero border: texel centres at (i + 1/2) / N, so
+// s = p N - 1/2, taps floor(s) and floor(s) + 1 with weights 1 - a and a
+// (a = s - floor(s)); floor(s) >= -1 and floor(s) + 1 <= N for p in [0, 1],
+// so only the two end texels can fall outside (weight zero).
+struct Taps1 {
+    int i0, i1;     // clamped indices
+    float w0, w1;   // in-bounds weights
 };
 
-__device__ __forceinline__ bool taps(float x, float y, int N, Taps& t) {
-    const float fN = float(N);
-    const float s = fmaf(x, fN, -0.5f), r = fmaf(y, fN, -0.5f);
-    const float fi = floorf(s), fj = floorf(r);
-    const float a = s - fi, b = r - fj;
-    const int i = int(fi), j = int(fj);
-    t.N = N;
-    t.wx0 = (unsigned(i) < unsigned(N)) ? 1.0f - a : 0.0f;
-    t.wx1 = (unsigned(i + 1) < unsigned(N)) ? a : 0.0f;
-    t.wy0 = (unsigned(j) < unsigned(N)) ? 1.0f - b : 0.0f;
-    t.wy1 = (unsigned(j + 1) < unsigned(N)) ? b : 0.0f;
+__device__ __forceinline__ Taps1 taps1(float p, int N) {
+    const float s = fmaf(p, float(N), -0.5f);
+    const float fi = floorf(s);
+    const float a = s - fi;
+    const int i = int(fi);
+    Taps1 t;
+    t.w0 = (i >= 0) ? 1.0f - a : 0.0f;
+    t.w1 = (i + 1 < N) ? a : 0.0f;
     t.i0 = max(i, 0);
     t.i1 = min(i + 1, N - 1);
-    t.j0 = max(j, 0);
-    t.j1 = min(j + 1, N - 1);
-    return (t.wx0 + t.wx1) * (t.wy0 + t.wy1) != 0.0f;
+    return t;
+}
+
+// Alg. 3's three fetches, after the query is clamped onto its triangle
+// (u, v >= 0, u + v <= 1):
+//   own    quad of h at (u, v) or (1 - u, 1 - v): inside [0, 1]^2, a 2x2 tap
+//          block per level;
+//   Next   quad of Next(h) at (v, -u) or (1 - v, 1 + u): the y coordinate lies
+//          u outside the quad, so only row 0 (row N - 1 when reflected) can
+//          be in bounds, with weight max(0, 1/2 - u N), and x = v (1 - v) is
+//          in [0, 1]: two taps per level;
+//   Prev   quad of Prev(h) at (-v, u) or (1 + v, 1 - u): only column 0
+//          (column N - 1) with weight max(0, 1/2 - v N), y = u (1 - u):
+//          two taps per level.
+// These are the bilinear taps of a zero-bordered sample written out for
+// the coordinates Alg. 3 produces; no tap with nonzero in-bounds weight is
+// left out.
+__device__ __forceinline__ float across_weight(float dist, int N) {
+    return fmaf(-dist, float(N), 0.5f);
+}
+
+// Taps of the own fetch at one level: byte offsets from the texture start
+// of (i0, j0), (i1, j0), (i0, j1), (i1, j1), their weights (level weight
+// included) and the level's share of the normalisation sum.  A tap of
+// weight zero is never loaded.
+struct OwnPlan {
+    uint32_t o[4];
+    float w[4];
+    float ws;
+};
+
+template <int TB>
+__device__ __forceinline__ OwnPlan own_plan(int n, int l, float x, float y, float wl) {
+    const int N = 1 << (n - l);
+    const Taps1 tx = taps1(x, N), ty = taps1(y, N);
+    const uint32_t lvl = level_texels(n, l) * uint32_t(TB);
+    const uint32_t r0 = lvl + uint32_t(ty.i0 * N) * TB, r1 = lvl + uint32_t(ty.i1 * N) * TB;
+    OwnPlan q;
+    q.o[0] = r0 + uint32_t(tx.i0) * TB;
+    q.o[1] = r0 + uint32_t(tx.i1) * TB;
+    q.o[2] = r1 + uint32_t(tx.i0) * TB;
+    q.o[3] = r1 + uint32_t(tx.i1) * TB;
+    const float y0 = ty.w0 * wl, y1 = ty.w1 * wl;
+    q.w[0] = y0 * tx.w0;
+    q.w[1] = y0 * tx.w1;
+    q.w[2] = y1 * tx.w0;
+    q.w[3] = y1 * tx.w1;
+    q.ws = wl * (tx.w0 + tx.w1) * (ty.w0 + ty.w1);
+    return q;
+}
+
+// Taps of a Next (ROW) or Prev fetch at one level: the two texels of the
+// row or column on the shared side, weights including the across weight
+// and the level weight (all zero when the query lies too far away).
+struct EdgePlan {
+    uint32_t o[2];
+    float w[2];
+    float ws;
+};
+
+template <int TB, bool ROW>
+__device__ __forceinline__ EdgePlan edge_plan(int n, int l, float dist, float along, bool flip, float wl) {
+    const int N = 1 << (n - l);
+    const float wa = across_weight(dist, N);
+    const float waw = wa > 0.0f ? wa * wl : 0.0f;
+    const Taps1 ta = taps1(flip ? 1.0f - along : along, N);
+    const int k = flip ? N - 1 : 0;
+    const uint32_t lvl = level_texels(n, l) * uint32_t(TB);
+    EdgePlan e;
+    e.o[0] = lvl + uint32_t(ROW ? k * N + ta.i0 : ta.i0 * N + k) * TB;
+    e.o[1] = lvl + uint32_t(ROW ? k * N + ta.i1 : ta.i1 * N + k) * TB;
+    e.w[0] = ta.w0 * waw;
+    e.w[1] = ta.w1 * waw;
+    e.ws = waw * (ta.w0 + ta.w1);
+    return e;
 }
 
 // Coordinates of one of Alg. 3's fetches in its quad (Alg. 2): reflected
@@ -266,11 +498,15 @@ __device__ __forceinline__ float footprint_log2(float f) {
     return (f > 0.0f) ? log2f(f) : -__int_as_float(0x7f800000);
 }
 
+// Streaming 16-byte query load: bypasses L1 and is marked first to leave L2.
 __device__ __forceinline__ int4 ld_query(const htex_query* q, int64_t i) {
     int4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(reinterpret_cast<const int4*>(q) + i));
+    asm volatile(
+        "{\n\t.reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+        "ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], pol;\n\t}"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(reinterpret_cast<const int4*>(q) + i));
     return r;
 }
 

@@ -41,7 +41,7 @@ struct htex_textures {
 };
 
 constexpr uint32_t kFlipBit = 0x80000000u;
-constexpr int kMaxLog2Res = 15;
+constexpr int kMaxLog2Res = 13;   // texture-relative byte offsets fit 32 bits
 
 int htex_elem_size(htex_dtype d);
 bool htex_dtype_valid(int32_t d);

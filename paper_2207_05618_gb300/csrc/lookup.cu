@@ -1,13 +1,22 @@
-// Forward filtered lookup (paper Section 4.4, Alg. 3 with Alg. 2) and the
-// htex_lookup entry point.
+// Forward filtered lookup (paper Section 4.4, Alg. 3 with Alg. 2), query
+// binning, and the htex_lookup entry point.
 //
-// One thread per query in a grid-stride loop over a persistent grid.  Per
+// One thread per query in a grid-stride loop over a persistent grid, with
+// the next query's load issued before the current one is filtered.  Per
 // query: one streaming 16-byte query load, one 16-byte packed record
 // (edges and Alg. 2 reflections of h, Next(h), Prev(h)), then up to three
-// fetches, each one or two levels of 2x2 border-aware taps; fetches whose
-// taps all fall outside their texture load nothing.  Two memory paths: the
-// pool staged in shared memory (small assets, many queries) or read
+// fetches, each one or two levels of 2x2 border-aware taps; a fetch whose
+// taps all fall outside its texture loads nothing.  Two memory paths: the
+// pool staged in shared memory (small assets, many queries) or gathered
 // through the read-only cache from global memory.
+//
+// Binning (HTEX_LOOKUP_BIN): a counting sort of the queries by halfedge
+// range (buckets of 2^shift consecutive halfedges, sized so the textures a
+// bucket touches fit in L2), so that queries sharing textures run close
+// together in time and their texel sectors are read from DRAM once.
+#include <algorithm>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "fetch.cuh"
@@ -19,41 +28,11 @@ struct FwdParams {
     int64_t n;
     float* out;
     int32_t* status;
+    const int32_t* idx;   // binned: original index of each sorted query
 };
 
-template <int DT, int C, class S>
-__device__ __forceinline__ void sample_acc(const Asset<S>& A, const TexRef& t, int l, float x, float y,
-                                           float wl, float (&acc)[C], float& W) {
-    Taps k;
-    if (!taps(x, y, 1 << (t.n - l), k)) return;
-    constexpr int TB = C * Fmt<DT>::ES;
-    using off_t = typename S::off_t;
-    const off_t lvl = off_t(t.off + level_bytes(t.n, l, TB));
-    float t00[C], t10[C], t01[C], t11[C];
-    load_texel<DT, C>(A.pool, lvl + off_t(k.j0 * k.N + k.i0) * TB, t00);
-    load_texel<DT, C>(A.pool, lvl + off_t(k.j0 * k.N + k.i1) * TB, t10);
-    load_texel<DT, C>(A.pool, lvl + off_t(k.j1 * k.N + k.i0) * TB, t01);
-    load_texel<DT, C>(A.pool, lvl + off_t(k.j1 * k.N + k.i1) * TB, t11);
-    const float sc = wl * t.scale;
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        const float r0 = fmaf(k.wx0, t00[c], k.wx1 * t10[c]);
-        const float r1 = fmaf(k.wx0, t01[c], k.wx1 * t11[c]);
-        acc[c] = fmaf(sc, fmaf(k.wy0, r0, k.wy1 * r1), acc[c]);
-    }
-    W = fmaf(wl, (k.wx0 + k.wx1) * (k.wy0 + k.wy1), W);
-}
-
-template <int DT, int C, class S>
-__device__ __forceinline__ void fetch_acc(const Asset<S>& A, uint32_t code, float a, float b, float lf,
-                                          float (&acc)[C], float& W) {
-    float x, y;
-    quad_coords(code, a, b, x, y);
-    const TexRef t = tex_ref<DT>(A, code & ~kFlipBit);
-    const Lod d = select_lod(lf, t.n);
-    sample_acc<DT, C>(A, t, d.l0, x, y, d.w0, acc, W);
-    if (d.l1 >= 0) sample_acc<DT, C>(A, t, d.l1, x, y, d.w1, acc, W);
-}
+// Coarsest level a fetch reads (its texels are the widest).
+__device__ __forceinline__ int coarsest(const Lod& d) { return d.l1 >= 0 ? d.l1 : d.l0; }
 
 template <int C>
 __device__ __forceinline__ void store_out(float* out, int64_t i, const float (&r)[C]) {
@@ -67,37 +46,202 @@ __device__ __forceinline__ void store_out(float* out, int64_t i, const float (&r
     }
 }
 
-template <int DT, int C, class S>
-__device__ __forceinline__ void lookup_one(const Asset<S>& A, const FwdParams& p, int64_t i) {
-    int h;
-    float u, v, f;
-    float r[C];
-    if (!decode_query(ld_query(p.q, i), A.H, h, u, v, f)) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) r[c] = __int_as_float(0x7fc00000);
-        if (p.status) atomicAdd(p.status, 1);
-    } else {
-        const uint4 rec = A.rec.ld16(typename S::off_t(h) * 16u);
-        const float lf = footprint_log2(f);
-        float acc[C];
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = 0.0f;
-        float W = 0.0f;
-        fetch_acc<DT, C>(A, rec.x, u, v, lf, acc, W);    // own quad at (u, v)
-        fetch_acc<DT, C>(A, rec.y, v, -u, lf, acc, W);   // Next(h)'s quad at (v, -u)
-        fetch_acc<DT, C>(A, rec.z, -v, u, lf, acc, W);   // Prev(h)'s quad at (-v, u)
-        const float inv = 1.0f / W;
-#pragma unroll
-        for (int c = 0; c < C; ++c) r[c] = acc[c] * inv;
-    }
-    store_out<C>(p.out, i, r);
+// The record of a query's halfedge (zeros when the id is out of range;
+// such a query is rejected before the record is used).
+template <class S>
+__device__ __forceinline__ uint4 record_of(const Asset<S>& A, int4 raw) {
+    if (unsigned(raw.x) >= unsigned(A.H)) return make_uint4(0, 0, 0, 0);
+    return A.rec.ld16(typename S::off_t(raw.x) * 16u);
 }
 
-template <int DT, int C>
-__global__ void __launch_bounds__(256) k_lookup_global(Asset<GlobalSpace> A, FwdParams p) {
+// The taps of one query, gathered in slots: up to 4 + 4 (own, two levels)
+// and 2 + 2 for each of Next and Prev.  With DEFER (packed texel formats
+// read from global memory) every load of nonzero weight is issued into a
+// raw register first and the decoding and weighting happen after all of
+// them are in flight; otherwise each slot is weighted as it is loaded.
+template <int DT, int C, bool DEFER>
+struct Gather {
+    static constexpr int K = 16;
+    Raw<DT, C> raw[DEFER ? K : 1];
+    float w[DEFER ? K : 1];
+    float acc[C];
+    float W = 0.0f;
+
+    __device__ __forceinline__ Gather() {
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+        // slots of parts the warp skips keep weight zero
+#pragma unroll
+        for (int k = 0; k < (DEFER ? K : 1); ++k) w[k] = 0.0f;
+    }
+
+    // slot k: load texel at byte offset o with data weight wd (W += ws done by caller)
+    template <int k, class S>
+    __device__ __forceinline__ void tap(const S& pool, typename S::off_t o, float wd) {
+        if constexpr (DEFER) {
+            w[k] = wd;
+            raw[k].load_if(pool, wd != 0.0f, o);
+        } else {
+            float t[C];
+            load_texel_if<DT, C>(pool, wd != 0.0f, o, t);
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = fmaf(wd, t[c], acc[c]);
+        }
+    }
+
+    __device__ __forceinline__ void finish() {
+        if constexpr (DEFER) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float t[C];
+                raw[k].decode(t);
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] = fmaf(w[k], t[c], acc[c]);
+            }
+        }
+    }
+};
+
+template <int DT, int C, int k0, bool DEFER, class S>
+__device__ __forceinline__ void own_taps(const Asset<S>& A, const TexRef& t, int l, float x, float y, float wl,
+                                         Gather<DT, C, DEFER>& g) {
+    using off_t = typename S::off_t;
+    constexpr int TB = C * Fmt<DT>::ES;
+    const OwnPlan q = own_plan<TB>(t.n, l, x, y, wl);
+    const float sc = Fmt<DT>::SCALED ? t.scale : 1.0f;
+    g.W += q.ws;
+    const off_t b = off_t(t.off);
+    g.template tap<k0 + 0>(A.pool, b + off_t(q.o[0]), q.w[0] * sc);
+    g.template tap<k0 + 1>(A.pool, b + off_t(q.o[1]), q.w[1] * sc);
+    g.template tap<k0 + 2>(A.pool, b + off_t(q.o[2]), q.w[2] * sc);
+    g.template tap<k0 + 3>(A.pool, b + off_t(q.o[3]), q.w[3] * sc);
+}
+
+template <int DT, int C, int k0, bool ROW, bool DEFER, class S>
+__device__ __forceinline__ void edge_taps(const Asset<S>& A, const TexRef& t, int l, float dist, float along,
+                                          bool flip, float wl, Gather<DT, C, DEFER>& g) {
+    using off_t = typename S::off_t;
+    constexpr int TB = C * Fmt<DT>::ES;
+    const EdgePlan e = edge_plan<TB, ROW>(t.n, l, dist, along, flip, wl);
+    const float sc = Fmt<DT>::SCALED ? t.scale : 1.0f;
+    g.W += e.ws;
+    const off_t b = off_t(t.off);
+    g.template tap<k0 + 0>(A.pool, b + off_t(e.o[0]), e.w[0] * sc);
+    g.template tap<k0 + 1>(A.pool, b + off_t(e.o[1]), e.w[1] * sc);
+}
+
+// Alg. 3 for one query: the own fetch (one or two levels) and the Next and
+// Prev fetches (one texel row / column per level); every load of nonzero
+// weight is issued without branching.  Parts that no lane of the warp
+// needs (a second level, an edge fetch with nothing in bounds) are
+// skipped warp-uniformly.
+template <int DT, int C, bool DEFER, class S>
+__device__ __forceinline__ void lookup_one(const Asset<S>& A, const FwdParams& p, int4 raw, uint4 rec,
+                                           int64_t dst) {
+    int h;
+    float u, v, f;
+    const bool ok = decode_query(raw, A.H, h, u, v, f);
+    if (!ok) {
+        u = 0.0f;
+        v = 0.0f;
+        f = 0.0f;
+        if (p.status) atomicAdd(p.status, 1);
+    }
+    const unsigned act = __activemask();
+    const float lf = footprint_log2(f);
+    const bool uni = A.uniform_log2n >= 0;
+    Gather<DT, C, DEFER> g;
+
+    // own quad at (u, v), through Alg. 2
+    const TexRef to = tex_ref<DT>(A, rec.x & ~kFlipBit);
+    const Lod d = select_lod(lf, to.n);
+    const bool fo = rec.x & kFlipBit;
+    const float x = fo ? 1.0f - u : u, y = fo ? 1.0f - v : v;
+    own_taps<DT, C, 0>(A, to, d.l0, x, y, ok ? d.w0 : 0.0f, g);
+    const bool two = ok && d.l1 >= 0;
+    if (__any_sync(act, two)) own_taps<DT, C, 4>(A, to, two ? d.l1 : d.l0, x, y, two ? d.w1 : 0.0f, g);
+
+    // Next(h)'s quad at (v, -u): the texel row on the shared side
+    const TexRef tn = tex_ref<DT>(A, rec.y & ~kFlipBit);
+    const Lod dn = uni ? d : select_lod(lf, tn.n);
+    const bool fn = rec.y & kFlipBit;
+    const bool nn = ok && across_weight(u, 1 << (tn.n - coarsest(dn))) > 0.0f;
+    if (__any_sync(act, nn)) {
+        edge_taps<DT, C, 8, true>(A, tn, dn.l0, u, v, fn, nn ? dn.w0 : 0.0f, g);
+        const bool n2 = nn && dn.l1 >= 0;
+        if (__any_sync(act, n2)) edge_taps<DT, C, 10, true>(A, tn, n2 ? dn.l1 : dn.l0, u, v, fn, n2 ? dn.w1 : 0.0f, g);
+    }
+
+    // Prev(h)'s quad at (-v, u): the texel column on the shared side
+    const TexRef tp = tex_ref<DT>(A, rec.z & ~kFlipBit);
+    const Lod dp = uni ? d : select_lod(lf, tp.n);
+    const bool fp = rec.z & kFlipBit;
+    const bool pp = ok && across_weight(v, 1 << (tp.n - coarsest(dp))) > 0.0f;
+    if (__any_sync(act, pp)) {
+        edge_taps<DT, C, 12, false>(A, tp, dp.l0, v, u, fp, pp ? dp.w0 : 0.0f, g);
+        const bool p2 = pp && dp.l1 >= 0;
+        if (__any_sync(act, p2)) edge_taps<DT, C, 14, false>(A, tp, p2 ? dp.l1 : dp.l0, v, u, fp, p2 ? dp.w1 : 0.0f, g);
+    }
+
+    g.finish();
+    const float inv = __frcp_rn(g.W);
+    float r[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) r[c] = ok ? g.acc[c] * inv : __int_as_float(0x7fc00000);
+    store_out<C>(p.out, dst, r);
+}
+
+template <bool BINNED>
+__device__ __forceinline__ int64_t dst_of(const FwdParams& p, int64_t i) {
+    return BINNED ? int64_t(__ldcs(p.idx + i)) : i;
+}
+
+// Grid-stride loop, software-pipelined: the query two iterations ahead and
+// (PREF_REC) the record one iteration ahead are in flight while the
+// current query's texels are gathered.
+template <int DT, int C, bool BINNED, bool PREF_REC, bool DEFER, class S>
+__device__ __forceinline__ void lookup_loop(const Asset<S>& A, const FwdParams& p) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < p.n; i += stride)
-        lookup_one<DT, C>(A, p, i);
+    int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i0 >= p.n) return;
+    int64_t i1 = i0 + stride;
+    int4 raw0 = ld_query(p.q, i0);
+    int64_t dst0 = dst_of<BINNED>(p, i0);
+    int4 raw1 = make_int4(-1, 0, 0, 0);
+    int64_t dst1 = 0;
+    if (i1 < p.n) {
+        raw1 = ld_query(p.q, i1);
+        dst1 = dst_of<BINNED>(p, i1);
+    }
+    uint4 rec0 = record_of(A, raw0);
+    while (true) {
+        const int64_t i2 = i1 + stride;
+        int4 raw2 = make_int4(-1, 0, 0, 0);
+        int64_t dst2 = 0;
+        if (i2 < p.n) {
+            raw2 = ld_query(p.q, i2);
+            dst2 = dst_of<BINNED>(p, i2);
+        }
+        uint4 rec1 = make_uint4(0, 0, 0, 0);
+        if (PREF_REC && i1 < p.n) rec1 = record_of(A, raw1);
+        lookup_one<DT, C, DEFER>(A, p, raw0, rec0, dst0);
+        if (i1 >= p.n) break;
+        if (!PREF_REC) rec1 = record_of(A, raw1);
+        raw0 = raw1;
+        dst0 = dst1;
+        rec0 = rec1;
+        raw1 = raw2;
+        dst1 = dst2;
+        i1 = i2;
+    }
+}
+
+constexpr int kGlobalThreads = 256;
+constexpr int kStagedThreads = 384;
+
+template <int DT, int C, bool BINNED>
+__global__ void __launch_bounds__(kGlobalThreads, 3) k_lookup_global(Asset<GlobalSpace> A, FwdParams p) {
+    lookup_loop<DT, C, BINNED, true, Raw<DT, C>::PACKED>(A, p);
 }
 
 // Shared-memory layout of a staged asset: records, headers, scales, pool,
@@ -122,9 +266,9 @@ __device__ __forceinline__ void stage16(uint8_t* dst, const void* src, uint32_t 
     for (uint32_t k = threadIdx.x; k < bytes / 16u; k += blockDim.x) d[k] = __ldg(s + k);
 }
 
-template <int DT, int C>
-__global__ void __launch_bounds__(256) k_lookup_staged(Asset<GlobalSpace> G, int32_t E, int64_t pool_bytes,
-                                                       FwdParams p) {
+template <int DT, int C, bool BINNED>
+__global__ void __launch_bounds__(kStagedThreads, 3) k_lookup_staged(Asset<GlobalSpace> G, int32_t E,
+                                                                  int64_t pool_bytes, FwdParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
     const StageLayout L = stage_layout(G.H, E, pool_bytes);
     stage16(smem + L.rec, G.rec.base, uint32_t(G.H) * 16u);
@@ -141,9 +285,99 @@ __global__ void __launch_bounds__(256) k_lookup_staged(Asset<GlobalSpace> G, int
     A.H = G.H;
     A.uniform_log2n = G.uniform_log2n;
     A.uniform_stride16 = G.uniform_stride16;
+    lookup_loop<DT, C, BINNED, false, false>(A, p);
+}
+
+// ------------------------------------------------------------------ binning
+
+constexpr int kBinThreads = 256;
+constexpr int kBinPerThread = 8;
+constexpr int kMaxBuckets = 4096;
+
+__device__ __forceinline__ uint32_t bucket_of(int32_t h, int32_t H, int shift, uint32_t invalid) {
+    return unsigned(h) < unsigned(H) ? uint32_t(h) >> shift : invalid;
+}
+
+// Pass 1: bucket sizes (shared-memory histogram per block, then global adds).
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(const htex_query* q, int64_t n, int32_t H, int shift,
+                                                           uint32_t B, uint32_t* counts) {
+    __shared__ uint32_t hist[kMaxBuckets + 1];
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < p.n; i += stride)
-        lookup_one<DT, C>(A, p, i);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int32_t h = __ldcs(reinterpret_cast<const int32_t*>(q + i));
+        atomicAdd(&hist[bucket_of(h, H, shift, B - 1)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x)
+        if (hist[b]) atomicAdd(&counts[b], hist[b]);
+}
+
+// Pass 2: every block derives the bucket offsets from the counts (an
+// exclusive scan of at most 4097 values), then places tiles of
+// kBinThreads * kBinPerThread queries: a block-local histogram and ranks,
+// one global reservation per (tile, bucket), and the writes of the
+// queries and their original indices into their bucket's range.
+__global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const htex_query* q, int64_t n, int32_t H, int shift,
+                                                             uint32_t B, const uint32_t* counts, uint32_t* taken,
+                                                             htex_query* qs, int32_t* idx) {
+    __shared__ uint32_t offset[kMaxBuckets + 1];
+    __shared__ uint32_t cnt[kMaxBuckets + 1];
+    __shared__ uint32_t base[kMaxBuckets + 1];
+    __shared__ uint32_t warp_tot[kBinThreads / 32];
+    // exclusive scan of counts: each thread a contiguous chunk
+    const uint32_t per = (B + kBinThreads - 1) / kBinThreads;
+    const uint32_t lo = min(B, threadIdx.x * per), hi = min(B, lo + per);
+    uint32_t run = 0;
+    for (uint32_t b = lo; b < hi; ++b) run += counts[b];
+    uint32_t incl = run;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t prefix = incl - run;
+    for (int w = 0; w < warp; ++w) prefix += warp_tot[w];
+    for (uint32_t b = lo; b < hi; ++b) {
+        offset[b] = prefix;
+        prefix += counts[b];
+    }
+    __syncthreads();
+
+    constexpr int TILE = kBinThreads * kBinPerThread;
+    for (int64_t t0 = int64_t(blockIdx.x) * TILE; t0 < n; t0 += int64_t(gridDim.x) * TILE) {
+        for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0;
+        __syncthreads();
+        int4 r[kBinPerThread];
+        uint32_t bk[kBinPerThread], rank[kBinPerThread];
+#pragma unroll
+        for (int k = 0; k < kBinPerThread; ++k) {
+            const int64_t i = t0 + int64_t(k) * kBinThreads + threadIdx.x;
+            if (i < n) {
+                r[k] = __ldcs(reinterpret_cast<const int4*>(q) + i);
+                bk[k] = bucket_of(r[k].x, H, shift, B - 1);
+                rank[k] = atomicAdd(&cnt[bk[k]], 1u);
+            }
+        }
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < B; b += blockDim.x)
+            if (cnt[b]) base[b] = offset[b] + atomicAdd(&taken[b], cnt[b]);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kBinPerThread; ++k) {
+            const int64_t i = t0 + int64_t(k) * kBinThreads + threadIdx.x;
+            if (i < n) {
+                const uint32_t pos = base[bk[k]] + rank[k];
+                reinterpret_cast<int4*>(qs)[pos] = r[k];
+                idx[pos] = int32_t(i);
+            }
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace htex
@@ -152,9 +386,9 @@ using namespace htex;
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr uint32_t kMaxStageBytes = 96u * 1024u;
 constexpr int64_t kMinStagedQueries = int64_t(1) << 20;
+constexpr int64_t kBucketTexelBytes = int64_t(32) << 20;
 
 Asset<GlobalSpace> global_asset(const htex_textures* t) {
     Asset<GlobalSpace> A;
@@ -169,58 +403,123 @@ Asset<GlobalSpace> global_asset(const htex_textures* t) {
 }
 
 template <class K>
-int resident_blocks(K kernel, size_t smem) {
+int resident_blocks(K kernel, int threads, size_t smem) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, smem) != cudaSuccess) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess) b = 1;
     return b > 0 ? b : 1;
 }
 
-template <int DT, int C>
+template <int DT, int C, bool BINNED>
 htex_status launch_fwd(const htex_textures* t, const FwdParams& p, uint32_t flags, cudaStream_t s) {
     const Asset<GlobalSpace> A = global_asset(t);
-    const int64_t want = (p.n + kThreads - 1) / kThreads;
     const StageLayout L = stage_layout(t->H, t->E, t->pool_bytes);
     const bool staged = !(flags & HTEX_LOOKUP_GLOBAL) && int64_t(L.total) <= int64_t(kMaxStageBytes) &&
                         p.n >= kMinStagedQueries;
     if (staged) {
-        auto k = k_lookup_staged<DT, C>;
+        auto k = k_lookup_staged<DT, C, BINNED>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.total)) != cudaSuccess)
             return HTEX_ERR_CUDA;
-        const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * resident_blocks(k, L.total));
-        k<<<unsigned(grid), kThreads, L.total, s>>>(A, t->E, t->pool_bytes, p);
+        const int64_t want = (p.n + kStagedThreads - 1) / kStagedThreads;
+        const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * resident_blocks(k, kStagedThreads, L.total));
+        k<<<unsigned(grid), kStagedThreads, L.total, s>>>(A, t->E, t->pool_bytes, p);
     } else {
-        auto k = k_lookup_global<DT, C>;
-        const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * resident_blocks(k, 0));
-        k<<<unsigned(grid), kThreads, 0, s>>>(A, p);
+        auto k = k_lookup_global<DT, C, BINNED>;
+        const int64_t want = (p.n + kGlobalThreads - 1) / kGlobalThreads;
+        const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * resident_blocks(k, kGlobalThreads, 0));
+        k<<<unsigned(grid), kGlobalThreads, 0, s>>>(A, p);
     }
     return cudaGetLastError() == cudaSuccess ? HTEX_OK : HTEX_ERR_CUDA;
 }
 
-template <int DT>
+template <int DT, bool BINNED>
 htex_status launch_fwd_c(const htex_textures* t, const FwdParams& p, uint32_t flags, cudaStream_t s) {
     switch (t->C) {
-    case 1: return launch_fwd<DT, 1>(t, p, flags, s);
-    case 2: return launch_fwd<DT, 2>(t, p, flags, s);
-    case 3: return launch_fwd<DT, 3>(t, p, flags, s);
-    case 4: return launch_fwd<DT, 4>(t, p, flags, s);
+    case 1: return launch_fwd<DT, 1, BINNED>(t, p, flags, s);
+    case 2: return launch_fwd<DT, 2, BINNED>(t, p, flags, s);
+    case 3: return launch_fwd<DT, 3, BINNED>(t, p, flags, s);
+    case 4: return launch_fwd<DT, 4, BINNED>(t, p, flags, s);
     }
     return HTEX_ERR_INVALID_ARG;
 }
 
+template <bool BINNED>
+htex_status launch_fwd_dt(const htex_textures* t, const FwdParams& p, uint32_t flags, cudaStream_t s) {
+    switch (t->dtype) {
+    case HTEX_F32: return launch_fwd_c<HTEX_F32, BINNED>(t, p, flags, s);
+    case HTEX_U8: return launch_fwd_c<HTEX_U8, BINNED>(t, p, flags, s);
+    case HTEX_F16: return launch_fwd_c<HTEX_F16, BINNED>(t, p, flags, s);
+    case HTEX_BF16: return launch_fwd_c<HTEX_BF16, BINNED>(t, p, flags, s);
+    case HTEX_E4M3: return launch_fwd_c<HTEX_E4M3, BINNED>(t, p, flags, s);
+    }
+    return HTEX_ERR_INVALID_ARG;
+}
+
+// Stream-ordered scratch from a library-owned pool per device that keeps
+// its memory between calls.
+cudaMemPool_t scratch_pool(int device) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    std::lock_guard<std::mutex> g(mu);
+    if (device < 0 || device >= 64) return nullptr;
+    if (!pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        uint64_t keep = ~uint64_t(0);
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[device] = p;
+    }
+    return pools[device];
+}
+
 }  // namespace
+
+// Halfedges per bucket (log2) so one bucket's textures take about
+// kBucketTexelBytes; returns -1 when the asset is too small to gain.
+int htex_bin_shift(const htex_textures* t) {
+    if (t->H <= 0 || t->pool_bytes <= 2 * kBucketTexelBytes) return -1;
+    const int64_t buckets = std::min<int64_t>(kMaxBuckets, (t->pool_bytes + kBucketTexelBytes - 1) / kBucketTexelBytes);
+    int shift = 0;
+    while ((int64_t(t->H) >> shift) + 1 > buckets) ++shift;
+    return shift;
+}
 
 htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,
                                uint32_t flags, htex_stream stream, int32_t* d_status) {
-    const FwdParams p{q, n, out, d_status};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    switch (t->dtype) {
-    case HTEX_F32: return launch_fwd_c<HTEX_F32>(t, p, flags, s);
-    case HTEX_U8: return launch_fwd_c<HTEX_U8>(t, p, flags, s);
-    case HTEX_F16: return launch_fwd_c<HTEX_F16>(t, p, flags, s);
-    case HTEX_BF16: return launch_fwd_c<HTEX_BF16>(t, p, flags, s);
-    case HTEX_E4M3: return launch_fwd_c<HTEX_E4M3>(t, p, flags, s);
+    const int shift = (flags & HTEX_LOOKUP_BIN) ? htex_bin_shift(t) : -1;
+    if (shift < 0 || n >= (int64_t(1) << 31)) return launch_fwd_dt<false>(t, FwdParams{q, n, out, d_status, nullptr}, flags, s);
+
+    const uint32_t B = uint32_t((int64_t(t->H) >> shift) + 2);   // + the bucket of invalid queries
+    const size_t qs_b = size_t(n) * 16, idx_b = size_t(n) * 4, cnt_b = size_t(B) * 4;
+    cudaMemPool_t pool = scratch_pool(t->device);
+    if (!pool) return HTEX_ERR_CUDA;
+    void* scratch = nullptr;
+    if (cudaMallocFromPoolAsync(&scratch, qs_b + idx_b + 2 * cnt_b + 64, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return HTEX_ERR_OUT_OF_MEMORY;
     }
-    return HTEX_ERR_INVALID_ARG;
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    htex_query* qs = reinterpret_cast<htex_query*>(base);
+    int32_t* idx = reinterpret_cast<int32_t*>(base + qs_b);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(base + qs_b + idx_b);
+    uint32_t* taken = counts + B;
+    htex_status st = HTEX_OK;
+    if (cudaMemsetAsync(counts, 0, 2 * cnt_b, s) != cudaSuccess) st = HTEX_ERR_CUDA;
+    if (st == HTEX_OK) {
+        const int64_t g1 = std::min<int64_t>((n + kBinThreads - 1) / kBinThreads, int64_t(t->num_sms) * 4);
+        k_bin_count<<<unsigned(g1), kBinThreads, 0, s>>>(q, n, t->H, shift, B, counts);
+        const int64_t tile = int64_t(kBinThreads) * kBinPerThread;
+        const int64_t g2 = std::min<int64_t>((n + tile - 1) / tile, int64_t(t->num_sms) * 2);
+        k_bin_scatter<<<unsigned(g2), kBinThreads, 0, s>>>(q, n, t->H, shift, B, counts, taken, qs, idx);
+        if (cudaGetLastError() != cudaSuccess) st = HTEX_ERR_CUDA;
+    }
+    if (st == HTEX_OK) st = launch_fwd_dt<true>(t, FwdParams{qs, n, out, d_status, idx}, flags, s);
+    cudaFreeAsync(scratch, s);
+    return st;
 }
 
 extern "C" htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,
@@ -232,6 +531,5 @@ extern "C" htex_status htex_lookup(const htex_textures* t, const htex_query* q, 
     if ((reinterpret_cast<uintptr_t>(q) & 15u) != 0) return HTEX_ERR_INVALID_ARG;
     const uintptr_t out_align = t->C == 4 ? 16u : (t->C == 2 ? 8u : 4u);
     if ((reinterpret_cast<uintptr_t>(out) & (out_align - 1)) != 0) return HTEX_ERR_INVALID_ARG;
-    if (flags & HTEX_LOOKUP_BIN) return HTEX_ERR_UNSUPPORTED;
     return htex_launch_lookup(t, q, n, out, flags, stream, d_status);
 }

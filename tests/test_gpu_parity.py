@@ -202,8 +202,28 @@ def test_asset_scale_small():
     _cmp(_gpu(tl, qs), oracle.lookup(mo, to, qs, nthreads=8))
 
 
+def test_binned_lookup_mid_asset():
+    """Binning reorders queries by halfedge range once the pool exceeds a
+    couple of L2-sized buckets (here about 97 MB of 32x32 RGBA8 texels):
+    results equal the unbinned kernel's bit for bit and the oracle's within
+    1e-5, including invalid queries (their own bucket) and a ragged count."""
+    gen = lambda: syn.cylinder(around=128, rows=60, seed=14)
+    mo, to, tl, *_ = _case(gen, _u(5), 4, "u8", hx.BUILD_MIPS | hx.MIRROR_BOUNDARY, seed=15)
+    assert tl.pool_bytes > (64 << 20)
+    h, u, v, f = syn.queries(mo.H, 300001, seed=16, footprint="loguniform")
+    hb, ub, vb, fb = syn.invalid_queries(mo.H)
+    qs = tuple(np.concatenate([a, b]) for a, b in zip((h, u, v, f), (hb, ub, vb, fb)))
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a = _gpu(tl, qs, flags=hx.LOOKUP_BIN, status=status)
+    b = _gpu(tl, qs)
+    np.testing.assert_array_equal(a, b)
+    assert int(status.item()) == 5
+    _cmp(a, oracle.lookup(mo, to, qs, nthreads=8))
+
+
 @pytest.mark.slow
-def test_asset_scale_full_sampled():
+@pytest.mark.parametrize("flags", [0, hx.LOOKUP_BIN])
+def test_asset_scale_full_sampled(flags):
     """The full asset-scale workload as the benchmark runs it (about 520k
     halfedges, 4.3 GB of level-0 RGBA8 texels, 16M queries in one launch);
     a sample of 100k outputs plus the first and last checked against the
@@ -216,7 +236,7 @@ def test_asset_scale_full_sampled():
     tl = hx.Textures.upload(ml, log2n, tex, 4, "u8", hx.BUILD_MIPS)
     n = 1 << 24
     qs = syn.queries(ml.H, n, seed=22, footprint="loguniform")
-    got = _gpu(tl, qs)
+    got = _gpu(tl, qs, flags=flags)
     sel = np.random.default_rng(1).choice(n, 100000, replace=False)
     sel[:2] = (0, n - 1)
     hs = qs[0][sel]

@@ -250,6 +250,36 @@ htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, in
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);
 
+/* ------------------------------------------------- allocation-free lookup */
+
+/* The paper has no counterpart to this call: it serves callers that must
+ * not allocate device memory.  Such callers include host applications or
+ * engines that own every device allocation and forbid the libraries they
+ * load to make their own, and frame loops that cannot absorb the
+ * device-wide synchronisation that cudaMalloc and cudaFree may cause.
+ *
+ * htex_lookup_noalloc computes exactly what htex_lookup with
+ * HTEX_LOOKUP_BIN computes (same arguments, same results), without any
+ * allocation: its scratch (the reordered queries, their original indices
+ * and the bucket counters) is one fixed device array inside the library,
+ * about 20 MiB, which every device that loads the library holds until the process
+ * exits.
+ *   n         at most htex_lookup_noalloc_max_queries() (1,048,576);
+ *             larger n returns HTEX_ERR_UNSUPPORTED before any device work
+ * The first call made with a given device current looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call on every stream shares the one array and the
+ * array keeps the previous call's contents (the call clears its counters
+ * itself), so calls whose device work overlaps (different streams without
+ * ordering between them) race and must not be issued.  The textures must
+ * live on the current device (HTEX_ERR_INVALID_ARG otherwise).
+ * Asynchronous on 'stream'. */
+htex_status htex_lookup_noalloc(const htex_textures* t, const htex_query* q, int64_t n, float* out,
+                                htex_stream stream, int32_t* d_status);
+
+/* Largest query count htex_lookup_noalloc accepts. */
+int64_t htex_lookup_noalloc_max_queries(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,8 @@ _SIGNATURES = {
     "htex_textures_destroy": ([P], None),
     "htex_lookup": ([P, P, I64, P, U32, P, P], I32),
     "htex_lookup_backward": ([P, P, I64, P, P, U32, P, P], I32),
+    "htex_lookup_noalloc": ([P, P, I64, P, P, P], I32),
+    "htex_lookup_noalloc_max_queries": ([], I64),
 }
 
 _lib = None

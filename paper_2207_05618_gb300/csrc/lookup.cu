@@ -533,3 +533,83 @@ extern "C" htex_status htex_lookup(const htex_textures* t, const htex_query* q, 
     if ((reinterpret_cast<uintptr_t>(out) & (out_align - 1)) != 0) return HTEX_ERR_INVALID_ARG;
     return htex_launch_lookup(t, q, n, out, flags, stream, d_status);
 }
+
+// ------------------------------------------------- allocation-free variant
+//
+// htex_lookup_noalloc: the binned lookup for callers that must not
+// allocate device memory, e.g. a host application or engine that owns
+// every device allocation and forbids its plug-ins to make their own, or a
+// frame loop that cannot absorb the device-wide synchronisation cudaMalloc
+// and cudaFree may cause.  Its scratch (sorted queries, their original
+// indices, bucket counters) lives in one fixed file-scope device array
+// that every device which loads this library holds until the process
+// exits.  Host code cannot use the array's name as a device address, so
+// the address is fetched once per device with cudaGetSymbolAddress.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxQueries = int64_t(1) << 20;
+constexpr size_t kNoAllocQueryBytes = size_t(kNoAllocMaxQueries) * 16;
+constexpr size_t kNoAllocIndexBytes = size_t(kNoAllocMaxQueries) * 4;
+constexpr size_t kNoAllocCountBytes = size_t(kMaxBuckets + 2) * 4;
+constexpr size_t kNoAllocBytes = kNoAllocQueryBytes + kNoAllocIndexBytes + 2 * kNoAllocCountBytes;
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch for the current device, looked up on
+// the first call made with that device current.
+htex_status noalloc_scratch(int device, uint8_t** out) {
+    static std::mutex mu;
+    static void* addr[64] = {};
+    if (device < 0 || device >= 64) return HTEX_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[device]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return HTEX_ERR_CUDA;
+        }
+        addr[device] = p;
+    }
+    *out = static_cast<uint8_t*>(addr[device]);
+    return HTEX_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t htex_lookup_noalloc_max_queries(void) { return kNoAllocMaxQueries; }
+
+extern "C" htex_status htex_lookup_noalloc(const htex_textures* t, const htex_query* q, int64_t n, float* out,
+                                           htex_stream stream, int32_t* d_status) {
+    if (!t || n < 0) return HTEX_ERR_INVALID_ARG;
+    if (n == 0) return HTEX_OK;
+    if (!q || !out) return HTEX_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(q) & 15u) != 0) return HTEX_ERR_INVALID_ARG;
+    const uintptr_t out_align = t->C == 4 ? 16u : (t->C == 2 ? 8u : 4u);
+    if ((reinterpret_cast<uintptr_t>(out) & (out_align - 1)) != 0) return HTEX_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxQueries) return HTEX_ERR_UNSUPPORTED;
+    int device = -1;
+    if (cudaGetDevice(&device) != cudaSuccess) return HTEX_ERR_CUDA;
+    if (device != t->device) return HTEX_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int shift = htex_bin_shift(t);
+    if (shift < 0) return launch_fwd_dt<false>(t, FwdParams{q, n, out, d_status, nullptr}, 0u, s);
+
+    uint8_t* base = nullptr;
+    htex_status st = noalloc_scratch(device, &base);
+    if (st != HTEX_OK) return st;
+    const uint32_t B = uint32_t((int64_t(t->H) >> shift) + 2);
+    htex_query* qs = reinterpret_cast<htex_query*>(base);
+    int32_t* idx = reinterpret_cast<int32_t*>(base + kNoAllocQueryBytes);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(base + kNoAllocQueryBytes + kNoAllocIndexBytes);
+    uint32_t* taken = counts + (kMaxBuckets + 2);
+    // the array keeps the previous call's contents: clear both counter sets
+    if (cudaMemsetAsync(counts, 0, 2 * kNoAllocCountBytes, s) != cudaSuccess) return HTEX_ERR_CUDA;
+    const int64_t g1 = std::min<int64_t>((n + kBinThreads - 1) / kBinThreads, int64_t(t->num_sms) * 4);
+    k_bin_count<<<unsigned(g1), kBinThreads, 0, s>>>(q, n, t->H, shift, B, counts);
+    const int64_t tile = int64_t(kBinThreads) * kBinPerThread;
+    const int64_t g2 = std::min<int64_t>((n + tile - 1) / tile, int64_t(t->num_sms) * 2);
+    k_bin_scatter<<<unsigned(g2), kBinThreads, 0, s>>>(q, n, t->H, shift, B, counts, taken, qs, idx);
+    if (cudaGetLastError() != cudaSuccess) return HTEX_ERR_CUDA;
+    return launch_fwd_dt<true>(t, FwdParams{qs, n, out, d_status, idx}, 0u, s);
+}

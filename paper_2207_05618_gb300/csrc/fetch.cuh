@@ -15,107 +15,43 @@ namespace htex {
 // ------------------------------------------------------------ memory spaces
 
 // Read-only global memory: texels and records through the non-coherent
-// (read-only) cache path.
+// (read-only) cache path.  The *_if loads touch memory only when p holds
+// and return zero otherwise (the compiler predicates them).
 struct GlobalSpace {
     using off_t = uint64_t;
     const uint8_t* base;
-    __device__ __forceinline__ uint4 ld16(off_t o) const { return __ldg(reinterpret_cast<const uint4*>(base + o)); }
-    __device__ __forceinline__ uint2 ld8(off_t o) const { return __ldg(reinterpret_cast<const uint2*>(base + o)); }
-    __device__ __forceinline__ uint32_t ld4(off_t o) const { return __ldg(reinterpret_cast<const unsigned int*>(base + o)); }
-    __device__ __forceinline__ uint32_t ld2(off_t o) const { return __ldg(reinterpret_cast<const unsigned short*>(base + o)); }
-    __device__ __forceinline__ uint32_t ld1(off_t o) const { return __ldg(reinterpret_cast<const unsigned char*>(base + o)); }
-    // Predicated loads: no memory access and a zero result when p is false.
-    __device__ __forceinline__ uint4 ld16_if(bool p, off_t o) const {
-        uint4 r = make_uint4(0u, 0u, 0u, 0u);
-        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
-            : "+r"(r.x), "+r"(r.y), "+r"(r.z), "+r"(r.w) : "l"(base + o), "r"(uint32_t(p)));
-        return r;
-    }
-    __device__ __forceinline__ uint2 ld8_if(bool p, off_t o) const {
-        uint2 r = make_uint2(0u, 0u);
-        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q ld.global.nc.v2.u32 {%0, %1}, [%2];\n\t}"
-            : "+r"(r.x), "+r"(r.y) : "l"(base + o), "r"(uint32_t(p)));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld4_if(bool p, off_t o) const {
-        uint32_t r = 0u;
-        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u32 %0, [%1];\n\t}"
-            : "+r"(r) : "l"(base + o), "r"(uint32_t(p)));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld2_if(bool p, off_t o) const {
-        unsigned short r = 0;
-        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u16 %0, [%1];\n\t}"
-            : "+h"(r) : "l"(base + o), "r"(uint32_t(p)));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld1_if(bool p, off_t o) const {
-        unsigned short r = 0;
-        asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.global.nc.u8 %0, [%1];\n\t}"
-            : "+h"(r) : "l"(base + o), "r"(uint32_t(p)));
-        return r & 0xffu;
-    }
+    template <class T>
+    __device__ __forceinline__ T at(off_t o) const { return __ldg(reinterpret_cast<const T*>(base + o)); }
+    __device__ __forceinline__ uint4 ld16(off_t o) const { return at<uint4>(o); }
+    __device__ __forceinline__ uint2 ld8(off_t o) const { return at<uint2>(o); }
+    __device__ __forceinline__ uint32_t ld4(off_t o) const { return at<unsigned int>(o); }
+    __device__ __forceinline__ uint32_t ld2(off_t o) const { return at<unsigned short>(o); }
+    __device__ __forceinline__ uint32_t ld1(off_t o) const { return at<unsigned char>(o); }
+    __device__ __forceinline__ uint4 ld16_if(bool p, off_t o) const { return p ? ld16(o) : make_uint4(0u, 0u, 0u, 0u); }
+    __device__ __forceinline__ uint2 ld8_if(bool p, off_t o) const { return p ? ld8(o) : make_uint2(0u, 0u); }
+    __device__ __forceinline__ uint32_t ld4_if(bool p, off_t o) const { return p ? ld4(o) : 0u; }
+    __device__ __forceinline__ uint32_t ld2_if(bool p, off_t o) const { return p ? ld2(o) : 0u; }
+    __device__ __forceinline__ uint32_t ld1_if(bool p, off_t o) const { return p ? ld1(o) : 0u; }
 };
 
-// Shared memory addressed by 32-bit shared-window addresses.
+// Shared memory: 'base' points into the kernel's dynamic shared buffer (the
+// compiler sees where it comes from and emits shared-window loads); offsets
+// are 32-bit.
 struct SharedSpace {
     using off_t = uint32_t;
-    uint32_t base;
-    __device__ __forceinline__ uint4 ld16(off_t o) const {
-        uint4 r;
-        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(base + o));
-        return r;
-    }
-    __device__ __forceinline__ uint2 ld8(off_t o) const {
-        uint2 r;
-        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(base + o));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld4(off_t o) const {
-        uint32_t r;
-        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(base + o));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld2(off_t o) const {
-        unsigned short r;
-        asm volatile("ld.shared.u16 %0, [%1];" : "=h"(r) : "r"(base + o));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld1(off_t o) const {
-        unsigned short r;
-        asm volatile("ld.shared.u8 %0, [%1];" : "=h"(r) : "r"(base + o));
-        return r & 0xffu;
-    }
-    __device__ __forceinline__ uint4 ld16_if(bool p, off_t o) const {
-        uint4 r = make_uint4(0u, 0u, 0u, 0u);
-        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
-                     : "+r"(r.x), "+r"(r.y), "+r"(r.z), "+r"(r.w) : "r"(base + o), "r"(uint32_t(p)));
-        return r;
-    }
-    __device__ __forceinline__ uint2 ld8_if(bool p, off_t o) const {
-        uint2 r = make_uint2(0u, 0u);
-        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q ld.shared.v2.u32 {%0, %1}, [%2];\n\t}"
-                     : "+r"(r.x), "+r"(r.y) : "r"(base + o), "r"(uint32_t(p)));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld4_if(bool p, off_t o) const {
-        uint32_t r = 0u;
-        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.u32 %0, [%1];\n\t}"
-                     : "+r"(r) : "r"(base + o), "r"(uint32_t(p)));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld2_if(bool p, off_t o) const {
-        unsigned short r = 0;
-        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.u16 %0, [%1];\n\t}"
-                     : "+h"(r) : "r"(base + o), "r"(uint32_t(p)));
-        return r;
-    }
-    __device__ __forceinline__ uint32_t ld1_if(bool p, off_t o) const {
-        unsigned short r = 0;
-        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q ld.shared.u8 %0, [%1];\n\t}"
-                     : "+h"(r) : "r"(base + o), "r"(uint32_t(p)));
-        return r & 0xffu;
-    }
+    const uint8_t* base;
+    template <class T>
+    __device__ __forceinline__ T at(off_t o) const { return *reinterpret_cast<const T*>(base + o); }
+    __device__ __forceinline__ uint4 ld16(off_t o) const { return at<uint4>(o); }
+    __device__ __forceinline__ uint2 ld8(off_t o) const { return at<uint2>(o); }
+    __device__ __forceinline__ uint32_t ld4(off_t o) const { return at<unsigned int>(o); }
+    __device__ __forceinline__ uint32_t ld2(off_t o) const { return at<unsigned short>(o); }
+    __device__ __forceinline__ uint32_t ld1(off_t o) const { return at<unsigned char>(o); }
+    __device__ __forceinline__ uint4 ld16_if(bool p, off_t o) const { return p ? ld16(o) : make_uint4(0u, 0u, 0u, 0u); }
+    __device__ __forceinline__ uint2 ld8_if(bool p, off_t o) const { return p ? ld8(o) : make_uint2(0u, 0u); }
+    __device__ __forceinline__ uint32_t ld4_if(bool p, off_t o) const { return p ? ld4(o) : 0u; }
+    __device__ __forceinline__ uint32_t ld2_if(bool p, off_t o) const { return p ? ld2(o) : 0u; }
+    __device__ __forceinline__ uint32_t ld1_if(bool p, off_t o) const { return p ? ld1(o) : 0u; }
 };
 
 // ---------------------------------------------------------------- decoding
@@ -435,8 +371,8 @@ __device__ __forceinline__ OwnPlan own_plan(int n, int l, float x, float y, floa
     return q;
 }
 
-// Taps of a Next (ROW) or Prev fetch at one level: the two texels of the
-// row or column on the shared side, weights including the across weight
+// Taps of a Next (row = true) or Prev fetch at one level: the two texels of
+// the row or column on the shared side, weights including the across weight
 // and the level weight (all zero when the query lies too far away).
 struct EdgePlan {
     uint32_t o[2];
@@ -444,17 +380,20 @@ struct EdgePlan {
     float ws;
 };
 
-template <int TB, bool ROW>
-__device__ __forceinline__ EdgePlan edge_plan(int n, int l, float dist, float along, bool flip, float wl) {
+template <int TB>
+__device__ __forceinline__ EdgePlan edge_plan(int n, int l, float dist, float along, bool flip, bool row,
+                                              float wl) {
     const int N = 1 << (n - l);
     const float wa = across_weight(dist, N);
     const float waw = wa > 0.0f ? wa * wl : 0.0f;
     const Taps1 ta = taps1(flip ? 1.0f - along : along, N);
     const int k = flip ? N - 1 : 0;
     const uint32_t lvl = level_texels(n, l) * uint32_t(TB);
+    // texel (i, k) of the row or (k, i) of the column, row-major j * N + i
+    const uint32_t stride_i = row ? 1u : uint32_t(N), fixed = row ? uint32_t(k * N) : uint32_t(k);
     EdgePlan e;
-    e.o[0] = lvl + uint32_t(ROW ? k * N + ta.i0 : ta.i0 * N + k) * TB;
-    e.o[1] = lvl + uint32_t(ROW ? k * N + ta.i1 : ta.i1 * N + k) * TB;
+    e.o[0] = lvl + (fixed + uint32_t(ta.i0) * stride_i) * TB;
+    e.o[1] = lvl + (fixed + uint32_t(ta.i1) * stride_i) * TB;
     e.w[0] = ta.w0 * waw;
     e.w[1] = ta.w1 * waw;
     e.ws = waw * (ta.w0 + ta.w1);
@@ -496,6 +435,11 @@ __device__ __forceinline__ bool decode_query(int4 raw, int32_t H, int& h, float&
 // log2 of the footprint, or -inf when level 0 is forced (footprint <= 0 or NaN).
 __device__ __forceinline__ float footprint_log2(float f) {
     return (f > 0.0f) ? log2f(f) : -__int_as_float(0x7f800000);
+}
+
+// Bring a future query's line into L2 (no register, no wait).
+__device__ __forceinline__ void prefetch_query(const htex_query* q, int64_t i) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const int4*>(q) + i));
 }
 
 // Streaming 16-byte query load: bypasses L1 and is marked first to leave L2.

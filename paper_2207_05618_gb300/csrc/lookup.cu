@@ -117,12 +117,12 @@ __device__ __forceinline__ void own_taps(const Asset<S>& A, const TexRef& t, int
     g.template tap<k0 + 3>(A.pool, b + off_t(q.o[3]), q.w[3] * sc);
 }
 
-template <int DT, int C, int k0, bool ROW, bool DEFER, class S>
+template <int DT, int C, int k0, bool DEFER, class S>
 __device__ __forceinline__ void edge_taps(const Asset<S>& A, const TexRef& t, int l, float dist, float along,
-                                          bool flip, float wl, Gather<DT, C, DEFER>& g) {
+                                          bool flip, bool row, float wl, Gather<DT, C, DEFER>& g) {
     using off_t = typename S::off_t;
     constexpr int TB = C * Fmt<DT>::ES;
-    const EdgePlan e = edge_plan<TB, ROW>(t.n, l, dist, along, flip, wl);
+    const EdgePlan e = edge_plan<TB>(t.n, l, dist, along, flip, row, wl);
     const float sc = Fmt<DT>::SCALED ? t.scale : 1.0f;
     g.W += e.ws;
     const off_t b = off_t(t.off);
@@ -130,11 +130,70 @@ __device__ __forceinline__ void edge_taps(const Asset<S>& A, const TexRef& t, in
     g.template tap<k0 + 1>(A.pool, b + off_t(e.o[1]), e.w[1] * sc);
 }
 
-// Alg. 3 for one query: the own fetch (one or two levels) and the Next and
-// Prev fetches (one texel row / column per level); every load of nonzero
-// weight is issued without branching.  Parts that no lane of the warp
-// needs (a second level, an edge fetch with nothing in bounds) are
-// skipped warp-uniformly.
+// One edge fetch (Next: row, dist u, along v; Prev: column, dist v, along
+// u), one or two levels, for the lanes with 'on' set.
+template <int DT, int C, int k0, bool L0, bool DEFER, class S>
+__device__ __forceinline__ void edge_fetch(const Asset<S>& A, unsigned act, bool on, const TexRef& t, const Lod& d,
+                                           float dist, float along, bool flip, bool row, Gather<DT, C, DEFER>& g) {
+    edge_taps<DT, C, k0>(A, t, L0 ? 0 : d.l0, dist, along, flip, row, on ? (L0 ? 1.0f : d.w0) : 0.0f, g);
+    if constexpr (!L0) {
+        const bool two = on && d.l1 >= 0;
+        if (__any_sync(act, two))
+            edge_taps<DT, C, k0 + 2>(A, t, two ? d.l1 : d.l0, dist, along, flip, row, two ? d.w1 : 0.0f, g);
+    }
+}
+
+// Alg. 3 for one query: the own fetch (one or two levels), then the Next
+// and Prev fetches (one texel row / column per level).  A lane needs both
+// edge fetches only within half a texel of the face centroid, so the lanes
+// of a warp share one edge pass, each running the edge it needs (Next if
+// any, else Prev); a second pass runs Prev for the lanes that need both.
+// Every load of nonzero weight is issued without branching; parts no lane
+// of the warp needs are skipped warp-uniformly.  L0: no lane of the warp
+// has a positive footprint, so every fetch is level 0 only.
+template <int DT, int C, bool L0, bool DEFER, class S>
+__device__ __forceinline__ void lookup_body(const Asset<S>& A, const FwdParams& p, unsigned act, bool ok, float u,
+                                            float v, float f, uint4 rec, int64_t dst) {
+    const bool uni = A.uniform_log2n >= 0;
+    const float lf = L0 ? -__int_as_float(0x7f800000) : footprint_log2(f);
+    Gather<DT, C, DEFER> g;
+
+    // own quad at (u, v), through Alg. 2
+    const TexRef to = tex_ref<DT>(A, rec.x & ~kFlipBit);
+    const Lod d = L0 ? Lod{0, -1, 1.0f, 0.0f} : select_lod(lf, to.n);
+    const bool fo = rec.x & kFlipBit;
+    const float x = fo ? 1.0f - u : u, y = fo ? 1.0f - v : v;
+    own_taps<DT, C, 0>(A, to, L0 ? 0 : d.l0, x, y, ok ? (L0 ? 1.0f : d.w0) : 0.0f, g);
+    if constexpr (!L0) {
+        const bool two = ok && d.l1 >= 0;
+        if (__any_sync(act, two)) own_taps<DT, C, 4>(A, to, two ? d.l1 : d.l0, x, y, two ? d.w1 : 0.0f, g);
+    }
+
+    // which edge fetches have taps in bounds (at the coarsest level read)
+    const TexRef tn = tex_ref<DT>(A, rec.y & ~kFlipBit);
+    const TexRef tp = tex_ref<DT>(A, rec.z & ~kFlipBit);
+    const Lod dn = (L0 || uni) ? d : select_lod(lf, tn.n);
+    const Lod dp = (L0 || uni) ? d : select_lod(lf, tp.n);
+    const bool nn = ok && across_weight(u, 1 << (tn.n - coarsest(dn))) > 0.0f;
+    const bool pp = ok && across_weight(v, 1 << (tp.n - coarsest(dp))) > 0.0f;
+
+    if (__any_sync(act, nn || pp)) {   // first edge pass: Next where needed, else Prev
+        const bool row = nn;
+        edge_fetch<DT, C, 8, L0>(A, act, nn || pp, row ? tn : tp, row ? dn : dp, row ? u : v, row ? v : u,
+                                 ((row ? rec.y : rec.z) & kFlipBit) != 0, row, g);
+    }
+    if (__any_sync(act, nn && pp))     // second pass: Prev for lanes that need both
+        edge_fetch<DT, C, 12, L0>(A, act, nn && pp, tp, dp, v, u, (rec.z & kFlipBit) != 0, false, g);
+
+    g.finish();
+    // an invalid query has every weight zero: W = 0, 1/W = inf, 0 * inf = NaN
+    const float inv = __frcp_rn(g.W);
+    float r[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) r[c] = g.acc[c] * inv;
+    store_out<C>(p.out, dst, r);
+}
+
 template <int DT, int C, bool DEFER, class S>
 __device__ __forceinline__ void lookup_one(const Asset<S>& A, const FwdParams& p, int4 raw, uint4 rec,
                                            int64_t dst) {
@@ -148,47 +207,8 @@ __device__ __forceinline__ void lookup_one(const Asset<S>& A, const FwdParams& p
         if (p.status) atomicAdd(p.status, 1);
     }
     const unsigned act = __activemask();
-    const float lf = footprint_log2(f);
-    const bool uni = A.uniform_log2n >= 0;
-    Gather<DT, C, DEFER> g;
-
-    // own quad at (u, v), through Alg. 2
-    const TexRef to = tex_ref<DT>(A, rec.x & ~kFlipBit);
-    const Lod d = select_lod(lf, to.n);
-    const bool fo = rec.x & kFlipBit;
-    const float x = fo ? 1.0f - u : u, y = fo ? 1.0f - v : v;
-    own_taps<DT, C, 0>(A, to, d.l0, x, y, ok ? d.w0 : 0.0f, g);
-    const bool two = ok && d.l1 >= 0;
-    if (__any_sync(act, two)) own_taps<DT, C, 4>(A, to, two ? d.l1 : d.l0, x, y, two ? d.w1 : 0.0f, g);
-
-    // Next(h)'s quad at (v, -u): the texel row on the shared side
-    const TexRef tn = tex_ref<DT>(A, rec.y & ~kFlipBit);
-    const Lod dn = uni ? d : select_lod(lf, tn.n);
-    const bool fn = rec.y & kFlipBit;
-    const bool nn = ok && across_weight(u, 1 << (tn.n - coarsest(dn))) > 0.0f;
-    if (__any_sync(act, nn)) {
-        edge_taps<DT, C, 8, true>(A, tn, dn.l0, u, v, fn, nn ? dn.w0 : 0.0f, g);
-        const bool n2 = nn && dn.l1 >= 0;
-        if (__any_sync(act, n2)) edge_taps<DT, C, 10, true>(A, tn, n2 ? dn.l1 : dn.l0, u, v, fn, n2 ? dn.w1 : 0.0f, g);
-    }
-
-    // Prev(h)'s quad at (-v, u): the texel column on the shared side
-    const TexRef tp = tex_ref<DT>(A, rec.z & ~kFlipBit);
-    const Lod dp = uni ? d : select_lod(lf, tp.n);
-    const bool fp = rec.z & kFlipBit;
-    const bool pp = ok && across_weight(v, 1 << (tp.n - coarsest(dp))) > 0.0f;
-    if (__any_sync(act, pp)) {
-        edge_taps<DT, C, 12, false>(A, tp, dp.l0, v, u, fp, pp ? dp.w0 : 0.0f, g);
-        const bool p2 = pp && dp.l1 >= 0;
-        if (__any_sync(act, p2)) edge_taps<DT, C, 14, false>(A, tp, p2 ? dp.l1 : dp.l0, v, u, fp, p2 ? dp.w1 : 0.0f, g);
-    }
-
-    g.finish();
-    const float inv = __frcp_rn(g.W);
-    float r[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) r[c] = ok ? g.acc[c] * inv : __int_as_float(0x7fc00000);
-    store_out<C>(p.out, dst, r);
+    if (__any_sync(act, f > 0.0f)) lookup_body<DT, C, false, DEFER>(A, p, act, ok, u, v, f, rec, dst);
+    else lookup_body<DT, C, true, DEFER>(A, p, act, ok, u, v, f, rec, dst);
 }
 
 template <bool BINNED>
@@ -196,9 +216,11 @@ __device__ __forceinline__ int64_t dst_of(const FwdParams& p, int64_t i) {
     return BINNED ? int64_t(__ldcs(p.idx + i)) : i;
 }
 
-// Grid-stride loop, software-pipelined: the query two iterations ahead and
-// (PREF_REC) the record one iteration ahead are in flight while the
-// current query's texels are gathered.
+// Grid-stride loop, software-pipelined.  Global path (PREF_REC): the query
+// two iterations ahead and the record one iteration ahead are in flight
+// while the current query's texels are gathered.  Staged path: the next
+// query in registers and the one three iterations ahead prefetched into
+// L2 (records are in shared memory).
 template <int DT, int C, bool BINNED, bool PREF_REC, bool DEFER, class S>
 __device__ __forceinline__ void lookup_loop(const Asset<S>& A, const FwdParams& p) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -213,26 +235,41 @@ __device__ __forceinline__ void lookup_loop(const Asset<S>& A, const FwdParams& 
         raw1 = ld_query(p.q, i1);
         dst1 = dst_of<BINNED>(p, i1);
     }
-    uint4 rec0 = record_of(A, raw0);
-    while (true) {
-        const int64_t i2 = i1 + stride;
-        int4 raw2 = make_int4(-1, 0, 0, 0);
-        int64_t dst2 = 0;
-        if (i2 < p.n) {
-            raw2 = ld_query(p.q, i2);
-            dst2 = dst_of<BINNED>(p, i2);
+    if constexpr (PREF_REC) {
+        uint4 rec0 = record_of(A, raw0);
+        while (true) {
+            const int64_t i2 = i1 + stride;
+            int4 raw2 = make_int4(-1, 0, 0, 0);
+            int64_t dst2 = 0;
+            if (i2 < p.n) {
+                raw2 = ld_query(p.q, i2);
+                dst2 = dst_of<BINNED>(p, i2);
+            }
+            uint4 rec1 = make_uint4(0, 0, 0, 0);
+            if (i1 < p.n) rec1 = record_of(A, raw1);
+            lookup_one<DT, C, DEFER>(A, p, raw0, rec0, dst0);
+            if (i1 >= p.n) break;
+            raw0 = raw1;
+            dst0 = dst1;
+            rec0 = rec1;
+            raw1 = raw2;
+            dst1 = dst2;
+            i1 = i2;
         }
-        uint4 rec1 = make_uint4(0, 0, 0, 0);
-        if (PREF_REC && i1 < p.n) rec1 = record_of(A, raw1);
-        lookup_one<DT, C, DEFER>(A, p, raw0, rec0, dst0);
-        if (i1 >= p.n) break;
-        if (!PREF_REC) rec1 = record_of(A, raw1);
-        raw0 = raw1;
-        dst0 = dst1;
-        rec0 = rec1;
-        raw1 = raw2;
-        dst1 = dst2;
-        i1 = i2;
+    } else {
+        while (true) {
+            if (i1 + 2 * stride < p.n) prefetch_query(p.q, i1 + 2 * stride);
+            lookup_one<DT, C, DEFER>(A, p, raw0, record_of(A, raw0), dst0);
+            if (i1 >= p.n) break;
+            raw0 = raw1;
+            dst0 = dst1;
+            const int64_t i2 = i1 + stride;
+            if (i2 < p.n) {
+                raw1 = ld_query(p.q, i2);
+                dst1 = dst_of<BINNED>(p, i2);
+            }
+            i1 = i2;
+        }
     }
 }
 
@@ -276,12 +313,11 @@ __global__ void __launch_bounds__(kStagedThreads, 3) k_lookup_staged(Asset<Globa
     stage16(smem + L.scale, G.scale.base, (uint32_t(E) * 4u + 15u) & ~15u);
     stage16(smem + L.pool, G.pool.base, uint32_t(pool_bytes));
     __syncthreads();
-    const uint32_t base = uint32_t(__cvta_generic_to_shared(smem));
     Asset<SharedSpace> A;
-    A.rec.base = base + L.rec;
-    A.hdr.base = base + L.hdr;
-    A.scale.base = base + L.scale;
-    A.pool.base = base + L.pool;
+    A.rec.base = smem + L.rec;
+    A.hdr.base = smem + L.hdr;
+    A.scale.base = smem + L.scale;
+    A.pool.base = smem + L.pool;
     A.H = G.H;
     A.uniform_log2n = G.uniform_log2n;
     A.uniform_stride16 = G.uniform_stride16;

@@ -213,6 +213,15 @@ htex_status htex_textures_info(const htex_textures* t, int32_t* channels, htex_d
 htex_status htex_textures_download_pool(const htex_textures* t, void* pool, float* scales,
                                         htex_stream stream);
 
+/* Overwrite 'bytes' bytes of the resident pool at byte 'offset' with 'src'
+ * (host or device memory), asynchronously on 'stream': in-place texel
+ * edits, e.g. the updates of a texture fit.  The bytes are stored values in
+ * the pool layout (for scaled formats, codes; the scales are unchanged).
+ * HTEX_ERR_INVALID_ARG if the range leaves the pool.  'src' must stay valid
+ * until 'stream' reaches the copy. */
+htex_status htex_textures_write_pool(const htex_textures* t, int64_t offset, int64_t bytes,
+                                     const void* src, htex_stream stream);
+
 void htex_textures_destroy(htex_textures* t);
 
 /* ---------------------------------------------------------------- lookups */
@@ -234,6 +243,23 @@ void htex_textures_destroy(htex_textures* t);
  * in FP32.  n = 0 is valid and launches nothing.  Asynchronous. */
 htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,
                         uint32_t flags, htex_stream stream, int32_t* d_status);
+
+/* htex_lookup on host buffers (the end-to-end path for callers whose
+ * queries and results live in host memory).
+ *   q    host [n] htex_query;  out  host [n][channels] float
+ * The queries go to the device and the results come back in chunks of
+ * 2,097,152, each chunk on one of three library-owned streams, so that the
+ * copy in of one chunk, the lookup of another and the copy out of a third
+ * overlap.  Copies overlap only from page-locked host memory (e.g.
+ * cudaHostAlloc, torch pin_memory); pageable buffers still give correct
+ * results.  The first call on a textures object creates its streams and
+ * about 200 MB of device staging (freed by htex_textures_destroy; returns
+ * HTEX_ERR_OUT_OF_MEMORY if that fails).  Ordered after earlier work on
+ * 'stream' and asynchronous: 'out' is complete once 'stream' is; 'q' and
+ * 'out' must stay valid until then.  Calls on one textures object are
+ * serialised on its internal streams.  Flags and d_status as htex_lookup. */
+htex_status htex_lookup_host(const htex_textures* t, const htex_query* q, int64_t n, float* out,
+                             uint32_t flags, htex_stream stream, int32_t* d_status);
 
 /* Gradient of L = sum_q sum_c grad_out[q][c] * lookup(q)[c] with respect to
  * every stored texel value (the decoded value T = code * scale for scaled

@@ -17,7 +17,7 @@ import numpy as np
 from ._lib import (BUILD_MIPS, DTYPES, ELEM_SIZE, FIX_CORNERS, LEVELS_GIVEN, LOOKUP_BIN,
                    LOOKUP_GLOBAL, MIRROR_BOUNDARY, HtexError, check, load)
 
-__all__ = ["Mesh", "Textures", "lookup", "lookup_backward", "pack_queries", "HtexLookup",
+__all__ = ["Mesh", "Textures", "lookup", "lookup_host", "lookup_backward", "pack_queries", "HtexLookup",
            "HtexError", "BUILD_MIPS", "MIRROR_BOUNDARY", "FIX_CORNERS", "LEVELS_GIVEN",
            "LOOKUP_BIN", "LOOKUP_GLOBAL"]
 
@@ -166,6 +166,20 @@ class Textures:
               "htex_textures_download_pool")
         return pool[:self.pool_bytes], scales[:self.E]
 
+    def write_pool(self, src, offset: int = 0, stream=None) -> None:
+        """Overwrite pool bytes from a CUDA tensor or host array (raw stored values)."""
+        import torch
+        if isinstance(src, torch.Tensor):
+            if not src.is_contiguous():
+                raise ValueError("src must be contiguous")
+            nbytes = src.numel() * src.element_size()
+            ptr = ctypes.c_void_p(src.data_ptr())
+        else:
+            arr = np.ascontiguousarray(src)
+            nbytes, ptr = arr.nbytes, _ptr(arr)
+        check(self._lib.htex_textures_write_pool(self._h, int(offset), int(nbytes), ptr, _stream(stream)),
+              "htex_textures_write_pool")
+
     @property
     def pool_elements(self) -> int:
         return self.pool_bytes // ELEM_SIZE[self.dtype]
@@ -212,6 +226,25 @@ def lookup(tex: Textures, queries, out=None, flags: int = 0, stream=None, status
     st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
     check(tex._lib.htex_lookup(tex._h, ctypes.c_void_p(queries.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
                                int(flags), _stream(stream), st), "htex_lookup")
+    return out
+
+
+def lookup_host(tex: Textures, queries, out=None, flags: int = 0, stream=None, status=None):
+    """htex_lookup_host: queries in host memory (int32 [n, 4], numpy or CPU
+    tensor, ideally pinned) -> float32 [n, channels] in host memory.  The
+    results are complete once 'stream' is synchronised."""
+    import torch
+    qt = torch.as_tensor(queries)
+    if qt.is_cuda or qt.dtype != torch.int32 or qt.dim() != 2 or qt.shape[1] != 4 or not qt.is_contiguous():
+        raise ValueError("queries must be a contiguous host int32 [n, 4] array")
+    n = qt.shape[0]
+    if out is None:
+        out = torch.empty((n, tex.channels), dtype=torch.float32, pin_memory=True)
+    if out.is_cuda or out.dtype != torch.float32 or tuple(out.shape) != (n, tex.channels) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous host float32 [n, channels] tensor")
+    st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    check(tex._lib.htex_lookup_host(tex._h, ctypes.c_void_p(qt.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
+                                    int(flags), _stream(stream), st), "htex_lookup_host")
     return out
 
 

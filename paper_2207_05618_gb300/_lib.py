@@ -53,9 +53,11 @@ _SIGNATURES = {
     "htex_textures_upload_pool": ([P, I32, I32, P, P, P, P, PP], I32),
     "htex_textures_info": ([P, P, P, P, P, P, P], I32),
     "htex_textures_download_pool": ([P, P, P, P], I32),
+    "htex_textures_write_pool": ([P, I64, I64, P, P], I32),
     "htex_textures_destroy": ([P], None),
     "htex_lookup": ([P, P, I64, P, U32, P, P], I32),
     "htex_lookup_backward": ([P, P, I64, P, P, U32, P, P], I32),
+    "htex_lookup_host": ([P, P, I64, P, U32, P, P], I32),
     "htex_lookup_noalloc": ([P, P, I64, P, P, P], I32),
     "htex_lookup_noalloc_max_queries": ([], I64),
 }

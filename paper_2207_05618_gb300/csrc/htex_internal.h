@@ -23,6 +23,8 @@ struct htex_mesh {
 //
 // Texture header of edge e (16 bytes): x = byte offset / 16, y = log2 N_e,
 // z = scale bits (float), w = 0.
+struct HostPath;   // staging for htex_lookup_host (host_path.cu)
+
 struct htex_textures {
     int32_t H = 0, E = 0, C = 0;
     htex_dtype dtype = HTEX_F32;
@@ -38,7 +40,10 @@ struct htex_textures {
     void* d_pool = nullptr;          // bytes [pool_bytes]
     int device = 0;
     int num_sms = 0;
+    HostPath* host_path = nullptr;   // created by the first htex_lookup_host
 };
+
+void htex_host_path_destroy(HostPath* hp);
 
 constexpr uint32_t kFlipBit = 0x80000000u;
 constexpr int kMaxLog2Res = 13;   // texture-relative byte offsets fit 32 bits

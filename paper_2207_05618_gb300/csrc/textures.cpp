@@ -518,8 +518,23 @@ extern "C" htex_status htex_textures_download_pool(const htex_textures* t, void*
     return HTEX_OK;
 }
 
+extern "C" htex_status htex_textures_write_pool(const htex_textures* t, int64_t offset, int64_t bytes,
+                                                const void* src, htex_stream stream) {
+    if (!t || offset < 0 || bytes < 0 || offset > t->pool_bytes || bytes > t->pool_bytes - offset)
+        return HTEX_ERR_INVALID_ARG;
+    if (bytes == 0) return HTEX_OK;
+    if (!src) return HTEX_ERR_INVALID_ARG;
+    if (cudaMemcpyAsync(static_cast<uint8_t*>(t->d_pool) + offset, src, size_t(bytes), cudaMemcpyDefault,
+                        reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return HTEX_ERR_CUDA;
+    }
+    return HTEX_OK;
+}
+
 extern "C" void htex_textures_destroy(htex_textures* t) {
     if (!t) return;
+    htex_host_path_destroy(t->host_path);
     cudaFree(t->d_rec);
     cudaFree(t->d_hdr);
     cudaFree(t->d_scale);

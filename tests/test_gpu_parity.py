@@ -264,3 +264,28 @@ def test_backward_matches_oracle_gradient(fmt, C):
     got = grad.cpu().numpy().astype(np.float64)
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= 1e-5 * max(scale, 1.0)
+
+
+# ------------------------------------------------------------------- host path
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_lookup_host_matches_device_lookup(pinned):
+    """htex_lookup_host (chunks of 2^21 over three internal streams) gives
+    the device lookup's results bit for bit, across chunk boundaries and a
+    ragged tail, from pinned and from pageable host memory."""
+    gen = lambda: syn.cylinder(around=32, rows=16, seed=11)
+    mo, to, tl, *_ = _case(gen, _u(6), 4, "u8", hx.BUILD_MIPS, seed=12)
+    n = 2 * (1 << 21) + 13
+    qs = syn.queries(mo.H, n, seed=13, footprint="loguniform")
+    qh = torch.from_numpy(hx.pack_queries(*qs))
+    if pinned:
+        qh = qh.pin_memory()
+    out = torch.empty((n, 4), dtype=torch.float32)
+    out = out.pin_memory() if pinned else out
+    hx.lookup_host(tl, qh, out=out)
+    torch.cuda.synchronize()
+    ref = hx.lookup(tl, qh.cuda()).cpu()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    sel = np.random.default_rng(2).choice(n, 20000, replace=False)
+    _cmp(out.numpy()[sel].astype(np.float64), oracle.lookup(mo, to, tuple(x[sel] for x in qs), nthreads=8))

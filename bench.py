@@ -46,6 +46,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cube", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
     p.add_argument("--rows", type=int, default=460, help="cylinder rows (460: the asset-scale mesh)")
     return p.parse_args()
 
@@ -388,6 +389,7 @@ def main():
 
     # the spec streaming case: the closed cube, 16x16 RGBA FP32, 2^24 queries
     cube = None if args.no_cube else cube_stream(hx, torch, stream, args)
+    serving = None if args.no_serving else serving_bench(hx, torch)
 
     peak, peak_src = hbm_peak()
     avg_ms = float(np.mean(launch_ms))
@@ -415,11 +417,103 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(mesh.H, mesh.E, nq, "bin" if args.bin else "none"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps * (1 if not args.bin else 3), "cube_stream": cube,
+            "gpu_launches": args.steps * (1 if not args.bin else 3), "cube_stream": cube, "serving": serving,
             "source_hash": source_hash(),
         }), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7):
+    """The serving workload: 8 resident assets (halfedges log-spaced over
+    [1k, 500k], 128^2..16^2 RGBA8 / FP16 textures), a Poisson stream of
+    requests of log-uniform 1k..4M queries with uniform asset tags, offered
+    at 'load' times the throughput of the plain per-request path, under a
+    device budget of 60% of the assets' bytes.  Reports p50/p99 latency and
+    aggregate lookups/s for the server and, on the same arrivals, for the
+    plain path (one htex_lookup_host per request in arrival order, all
+    assets resident)."""
+    import htex_synth as syn
+    from paper_2207_05618_gb300 import serve
+    specs = syn.serving_assets()
+    assets = []
+    for a in specs:
+        fs, fv, V = a["faces"]
+        mesh = hx.Mesh(fs, fv, V)
+        log2n = np.full(mesh.E, a["log2n"], np.int32)
+        tex = (syn.texels_u8 if a["dtype"] == "u8" else syn.texels_f32)(log2n, 4, seed=a["seed"])
+        pool, scales = hx.Textures.prepare(mesh, log2n, tex, 4, a["dtype"], hx.BUILD_MIPS | hx.MIRROR_BOUNDARY)
+        alone = hx.Textures.upload_pool(mesh, log2n, pool, scales, 4, a["dtype"])
+        assets.append({"mesh": mesh, "log2n": log2n, "pool": pool, "scales": scales, "dtype": a["dtype"],
+                       "alone": alone})
+    total = sum(a["alone"].device_bytes for a in assets)
+    qmax = 4_000_000
+    qpool = []
+    for k, a in enumerate(assets):
+        q = torch.from_numpy(hx.pack_queries(*syn.queries(a["mesh"].H, qmax, seed=300 + k,
+                                                          footprint="loguniform"))).pin_memory()
+        qpool.append(q)
+    out_arena = torch.empty((qmax, 4), dtype=torch.float32).pin_memory()
+    rng = np.random.default_rng(9)
+
+    def qsrc(a, n):
+        off = int(rng.integers(0, qmax - n + 1))
+        return qpool[a].data_ptr() + off * 16
+
+    # plain path throughput, requests back to back (sets the offered load)
+    _, sizes, tags = syn.poisson_requests(n_requests, 1.0, len(assets), seed=11)
+    stream = torch.cuda.current_stream()
+    warm = min(50, n_requests)
+    for k in range(warm):
+        n = int(sizes[k])
+        hx.lookup_host(assets[tags[k]]["alone"], qpool[tags[k]][:n], out=out_arena[:n], stream=stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for k in range(n_requests):
+        n = int(sizes[k])
+        hx.lookup_host(assets[tags[k]]["alone"], qpool[tags[k]][:n], out=out_arena[:n], stream=stream)
+    torch.cuda.synchronize()
+    plain_rate = float(sizes.sum()) / (time.perf_counter() - t)
+    rate = load * plain_rate / float(sizes.mean())
+    arrivals, sizes, tags = syn.poisson_requests(n_requests, rate, len(assets), seed=12)
+
+    # the plain path on these arrivals: one request at a time, first come first served
+    lat_plain = np.zeros(n_requests)
+    t0 = time.perf_counter()
+    for k in range(n_requests):
+        while time.perf_counter() < t0 + arrivals[k]:
+            pass
+        n = int(sizes[k])
+        hx.lookup_host(assets[tags[k]]["alone"], qpool[tags[k]][:n], out=out_arena[:n], stream=stream)
+        stream.synchronize()
+        lat_plain[k] = time.perf_counter() - (t0 + arrivals[k])
+    wall_plain = time.perf_counter() - t0
+    for a in assets:
+        a["alone"].close()
+
+    pct = lambda x, p: float(np.percentile(x, p) * 1e3)
+
+    def run_server(budget):
+        server = serve.Server(int(budget), batch_queries=1 << 22, batch_slots=3, max_items=256,
+                              request_chunk=1 << 20)
+        for a in assets:
+            server.add_asset(a["mesh"], a["log2n"], a["pool"], a["scales"], 4, a["dtype"])
+        lat, wall = serve.replay(server, arrivals, sizes, tags, qsrc, lambda k, a, n: out_arena.data_ptr())
+        st = server.stats()
+        server.close()
+        return {"budget_bytes": int(budget), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                "lookups_per_s": float(sizes.sum()) / wall, "batches": st["batches"], "uploads": st["uploads"],
+                "evictions": st["evictions"]}
+
+    res = run_server(0.6 * total)
+    res.update({"requests": int(n_requests), "offered_load": load,
+                "offered_lookups_per_s": float(rate * sizes.mean()), "assets": len(assets),
+                "asset_bytes": int(total),
+                "all_resident": run_server(2 * total),
+                "plain_path": {"p50_ms": pct(lat_plain, 50), "p99_ms": pct(lat_plain, 99),
+                               "lookups_per_s": float(sizes.sum()) / wall_plain,
+                               "back_to_back_lookups_per_s": plain_rate, "all_resident": True}})
+    return res
 
 
 def cube_stream(hx, torch, stream, args):

@@ -234,3 +234,35 @@ def invalid_queries(H):
     v = np.array([0.2, 0.2, 0.2, 0.3, 0.9, -1.0, 0.1, np.inf], np.float32)
     f = np.array([0, 0, 0, 0, 0, -1.0, np.nan, np.inf], np.float32)
     return h, u, v, f
+
+
+def cylinder_with_halfedges(target_H, seed=0):
+    """An open cylinder (splits and merges as `cylinder`) with about target_H halfedges."""
+    around = max(8, int(round((target_H / 4.5) ** 0.5)))
+    rows = max(2, int(round(target_H / (4.53 * around))))
+    return cylinder(around=around, rows=rows, seed=seed)
+
+
+def serving_assets(count=8, h_lo=1_000, h_hi=500_000):
+    """Serving workload assets: halfedge counts log-spaced over [h_lo, h_hi]
+    (both ends included); texture resolution 128, 128, 64, 64, 32, 32, 16, 16
+    from the smallest mesh up (total texels stay a few GB), formats
+    alternating RGBA8 / FP16.  Returns a list of dicts."""
+    hs = np.exp(np.linspace(np.log(h_lo), np.log(h_hi), count))
+    res = [128, 128, 64, 64, 32, 32, 16, 16]
+    out = []
+    for k, H in enumerate(hs):
+        fs, fv, V, _ = cylinder_with_halfedges(H, seed=100 + k)
+        out.append({"faces": (fs, fv, V), "log2n": int(np.log2(res[k % len(res)])),
+                    "dtype": "u8" if k % 2 == 0 else "f16", "seed": 200 + k})
+    return out
+
+
+def poisson_requests(count, rate, num_assets, lo=1_000, hi=4_000_000, seed=0):
+    """Request stream: arrival times of a Poisson process with 'rate'
+    requests/s, sizes log-uniform over [lo, hi] queries, uniform asset tags."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), count)).astype(np.int64)
+    assets = rng.integers(0, num_assets, count)
+    return arrivals - arrivals[0], sizes, assets

@@ -276,6 +276,78 @@ htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, in
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A lookup server: many assets kept resident under a device-memory budget
+ * and requests of uneven sizes from different assets served by continuous
+ * batching.  The paper renders one asset per frame; this serves the same
+ * per-query computation (Alg. 3) to a stream of requests.  A scheduler
+ * thread owned by the server
+ *   - uploads an asset when a request needs it and it fits the budget,
+ *     evicting the least recently used assets that no admitted request
+ *     still needs; requests whose asset does not fit yet wait (later
+ *     requests whose asset fits go ahead);
+ *   - fills each free batch slot from the admitted requests in arrival
+ *     order, at most request_chunk queries of one request per batch, so a
+ *     request that arrives while others run joins the next batch;
+ *   - launches a batch as an instantiated CUDA graph (descriptor table
+ *     copy, then one persistent kernel per texel format pulling 4096-query
+ *     tiles of any request), with the query and result copies around it.
+ * Results are those htex_lookup gives for the same queries (each query is
+ * computed by the same code, whatever shares its batch).
+ * Buffers: queries and results live in host memory (page-locked for copy
+ * speed) and must stay valid until the request completes. */
+typedef struct htex_server htex_server;
+
+typedef struct {
+    int64_t budget_bytes;   /* device bytes for resident assets                    */
+    int64_t batch_queries;  /* queries per batch (staging per slot: 32 B x this)   */
+    int32_t batch_slots;    /* batches in flight, 1..8                             */
+    int32_t max_items;      /* request chunks per batch, 1..256                    */
+    int64_t request_chunk;  /* most queries of one request in one batch            */
+} htex_server_config;
+
+typedef struct {
+    int64_t completed;       /* requests completed                  */
+    int64_t queries;         /* queries launched                    */
+    int64_t batches;         /* batches launched                    */
+    int64_t uploads;         /* asset uploads (admissions)          */
+    int64_t evictions;       /* assets evicted to make room         */
+    int64_t resident_bytes;  /* device bytes of resident assets now */
+} htex_server_stats;
+
+/* Create a server on the current device (allocates its staging, streams
+ * and graphs' buffers, starts its thread). */
+htex_status htex_server_create(const htex_server_config* cfg, htex_server** out);
+
+/* Register an asset from a prepared pool (htex_textures_prepare layout;
+ * scales required for scaled formats).  The pool is copied into page-locked
+ * host memory owned by the server; the asset becomes resident on demand.
+ * HTEX_ERR_OUT_OF_MEMORY if it alone exceeds the budget. */
+htex_status htex_server_add_asset(htex_server* s, const htex_mesh* m, int32_t channels, htex_dtype dtype,
+                                  const int32_t* log2_res, const void* pool, const float* scales,
+                                  int32_t* asset_id);
+
+/* Queue n queries (host) against an asset; results go to out (host,
+ * [n][channels] float).  Returns at once with the request's id. */
+htex_status htex_server_submit(htex_server* s, int32_t asset_id, const htex_query* q, int64_t n,
+                               float* out, int64_t* request_id);
+
+/* Take up to 'capacity' completed requests: their ids and latencies in
+ * seconds (submission to observed completion).  Returns the server's
+ * sticky error, if any. */
+htex_status htex_server_poll(htex_server* s, int64_t* ids, double* latency_s, int32_t capacity,
+                             int32_t* count);
+
+/* Wait until every submitted request has completed, at most timeout_s
+ * seconds (HTEX_ERR_TIMEOUT when the wait runs out). */
+htex_status htex_server_drain(htex_server* s, double timeout_s);
+
+htex_status htex_server_get_stats(htex_server* s, htex_server_stats* st);
+
+/* Stop the thread, wait for the device work and free everything. */
+void htex_server_destroy(htex_server* s);
+
 /* ------------------------------------------------- allocation-free lookup */
 
 /* The paper has no counterpart to this call: it serves callers that must

@@ -58,6 +58,13 @@ _SIGNATURES = {
     "htex_lookup": ([P, P, I64, P, U32, P, P], I32),
     "htex_lookup_backward": ([P, P, I64, P, P, U32, P, P], I32),
     "htex_lookup_host": ([P, P, I64, P, U32, P, P], I32),
+    "htex_server_create": ([P, PP], I32),
+    "htex_server_add_asset": ([P, P, I32, I32, P, P, P, P], I32),
+    "htex_server_submit": ([P, I32, P, I64, P, P], I32),
+    "htex_server_poll": ([P, P, P, I32, P], I32),
+    "htex_server_drain": ([P, ctypes.c_double], I32),
+    "htex_server_get_stats": ([P, P], I32),
+    "htex_server_destroy": ([P], None),
     "htex_lookup_noalloc": ([P, P, I64, P, P, P], I32),
     "htex_lookup_noalloc_max_queries": ([], I64),
 }

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "htex.h"
 
 // Host-side halfedge mesh: the six operators of the paper's halfedge
@@ -41,9 +43,38 @@ struct htex_textures {
     int device = 0;
     int num_sms = 0;
     HostPath* host_path = nullptr;   // created by the first htex_lookup_host
+    cudaStream_t free_stream = nullptr;  // set: buffers came from a pool, freed stream-ordered here
 };
 
 void htex_host_path_destroy(HostPath* hp);
+
+// Host-side arrays of a resident asset: packed records, headers, scales
+// (padded to whole 16-byte words) and layout facts.
+struct HtexAssetArrays {
+    std::vector<int32_t> rec;    // 4 per halfedge
+    std::vector<int32_t> hdr;    // 4 per edge
+    std::vector<float> scale;    // per edge, padded
+    int32_t H = 0, E = 0, C = 0;
+    htex_dtype dtype = HTEX_F32;
+    int32_t uniform_log2n = -1, max_log2n = 0;
+    int64_t uniform_stride = 0, pool_bytes = 0;
+};
+
+// Build the arrays (no GPU work).
+htex_status htex_asset_arrays(const htex_mesh* m, int32_t C, htex_dtype dtype, const int32_t* log2n,
+                              const float* scales, HtexAssetArrays* out);
+// Allocate the device memory of an asset described by 'a' on the current
+// device (no copies); device_bytes counts it.
+htex_status htex_asset_allocate(const HtexAssetArrays& a, htex_textures** out);
+// Same, from a memory pool, stream-ordered on 'stream' (the buffers are
+// released stream-ordered on that stream by htex_textures_destroy).
+htex_status htex_asset_allocate_async(const HtexAssetArrays& a, cudaMemPool_t pool, cudaStream_t stream,
+                                      htex_textures** out);
+// Device bytes an asset described by 'a' occupies.
+int64_t htex_asset_device_bytes(const HtexAssetArrays& a);
+// Enqueue the copies of records, headers, scales and the pool (host
+// buffers must stay valid until 'stream' has run them).
+htex_status htex_asset_copy_async(const HtexAssetArrays& a, const void* pool, htex_textures* t, cudaStream_t stream);
 
 constexpr uint32_t kFlipBit = 0x80000000u;
 constexpr int kMaxLog2Res = 13;   // texture-relative byte offsets fit 32 bits

@@ -370,69 +370,140 @@ htex_status cuda_fail(htex_textures* t) {
     return HTEX_ERR_CUDA;
 }
 
-htex_status upload_prepared(const htex_mesh* m, int32_t C, htex_dtype dtype, const int32_t* log2n,
-                            const void* pool, const float* scales, cudaStream_t stream,
-                            htex_textures** out) {
+}  // namespace
+
+htex_status htex_asset_arrays(const htex_mesh* m, int32_t C, htex_dtype dtype, const int32_t* log2n,
+                              const float* scales, HtexAssetArrays* out) {
+    HtexAssetArrays& A = *out;
     const int32_t H = m->H, E = m->E;
     std::vector<int64_t> boff(size_t(E) + 1);
-    const int64_t pool_bytes = htex_pool_offsets(E, log2n, C, dtype, boff.data());
+    A.pool_bytes = htex_pool_offsets(E, log2n, C, dtype, boff.data());
     if (boff[E] / 16 >= (int64_t(1) << 32)) return HTEX_ERR_UNSUPPORTED;  // header offsets are 32-bit x 16 B
-
+    A.H = H;
+    A.E = E;
+    A.C = C;
+    A.dtype = dtype;
     // per-halfedge lookup records: the edge and Alg. 2 reflection of h, Next(h), Prev(h)
-    std::vector<int32_t> rec(size_t(H) * 4);
+    A.rec.assign(size_t(H) * 4, 0);
     auto code = [&](int32_t g) { return uint32_t(m->edge[g]) | (g < m->twin[g] ? kFlipBit : 0u); };
     for (int32_t h = 0; h < H; ++h) {
-        rec[4 * size_t(h) + 0] = int32_t(code(h));
-        rec[4 * size_t(h) + 1] = int32_t(code(m->next[h]));
-        rec[4 * size_t(h) + 2] = int32_t(code(m->prev[h]));
-        rec[4 * size_t(h) + 3] = m->face[h];
+        A.rec[4 * size_t(h) + 0] = int32_t(code(h));
+        A.rec[4 * size_t(h) + 1] = int32_t(code(m->next[h]));
+        A.rec[4 * size_t(h) + 2] = int32_t(code(m->prev[h]));
+        A.rec[4 * size_t(h) + 3] = m->face[h];
     }
-    std::vector<int32_t> hdr(size_t(E) * 4);
-    std::vector<float> sc(size_t(E), 1.0f);
+    A.hdr.assign(size_t(E) * 4, 0);
+    A.scale.assign((size_t(E) + 3) & ~size_t(3), 1.0f);   // whole 16-byte words (shared-memory staging)
     int32_t uniform = E > 0 ? log2n[0] : 0, maxn = 0;
     for (int32_t e = 0; e < E; ++e) {
-        if (scales) sc[e] = scales[e];
-        float s = sc[e];
-        hdr[4 * size_t(e) + 0] = int32_t(uint32_t(boff[e] / 16));
-        hdr[4 * size_t(e) + 1] = log2n[e];
-        std::memcpy(&hdr[4 * size_t(e) + 2], &s, 4);
-        hdr[4 * size_t(e) + 3] = 0;
+        if (scales) A.scale[e] = scales[e];
+        const float sv = A.scale[e];
+        A.hdr[4 * size_t(e) + 0] = int32_t(uint32_t(boff[e] / 16));
+        A.hdr[4 * size_t(e) + 1] = log2n[e];
+        std::memcpy(&A.hdr[4 * size_t(e) + 2], &sv, 4);
         if (log2n[e] != uniform) uniform = -1;
         maxn = log2n[e] > maxn ? log2n[e] : maxn;
     }
-    sc.resize((size_t(E) + 3) & ~size_t(3), 1.0f);  // whole 16-byte words (shared-memory staging)
-    const size_t rec_b = rec.size() * 4, hdr_b = hdr.size() * 4, sc_b = sc.size() * 4;
-    const int64_t need = int64_t(rec_b + hdr_b + sc_b) + pool_bytes;
+    A.uniform_log2n = uniform;
+    A.max_log2n = maxn;
+    A.uniform_stride = (uniform >= 0 && E > 0) ? boff[1] - boff[0] : 0;
+    return HTEX_OK;
+}
 
+int64_t htex_asset_device_bytes(const HtexAssetArrays& a) {
+    return int64_t(a.rec.size() + a.hdr.size() + a.scale.size()) * 4 + a.pool_bytes;
+}
+
+htex_status htex_asset_allocate(const HtexAssetArrays& a, htex_textures** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(nullptr);
-    size_t free_b = 0, total_b = 0;
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return cuda_fail(nullptr);
-    if (need + (int64_t(64) << 20) > int64_t(free_b)) return HTEX_ERR_OUT_OF_MEMORY;
-
     htex_textures* t = new (std::nothrow) htex_textures;
     if (!t) return HTEX_ERR_OUT_OF_MEMORY;
-    t->H = H;
-    t->E = E;
-    t->C = C;
-    t->dtype = dtype;
-    t->uniform_log2n = uniform;
-    t->uniform_stride = (uniform >= 0 && E > 0) ? boff[1] - boff[0] : 0;
-    t->pool_bytes = pool_bytes;
-    t->max_log2n = maxn;
-    t->has_scales = is_scaled(dtype);
+    t->H = a.H;
+    t->E = a.E;
+    t->C = a.C;
+    t->dtype = a.dtype;
+    t->uniform_log2n = a.uniform_log2n;
+    t->uniform_stride = a.uniform_stride;
+    t->pool_bytes = a.pool_bytes;
+    t->max_log2n = a.max_log2n;
+    t->has_scales = is_scaled(a.dtype);
     t->device = dev;
     cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaMalloc(&t->d_rec, rec_b) != cudaSuccess) return cuda_fail(t);
-    if (cudaMalloc(&t->d_hdr, hdr_b ? hdr_b : 16) != cudaSuccess) return cuda_fail(t);
-    if (cudaMalloc(&t->d_scale, sc_b ? sc_b : 16) != cudaSuccess) return cuda_fail(t);
-    if (cudaMalloc(&t->d_pool, size_t(pool_bytes > 0 ? pool_bytes : 16)) != cudaSuccess) return cuda_fail(t);
-    t->device_bytes = need;
-    if (cudaMemcpyAsync(t->d_rec, rec.data(), rec_b, cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-        (hdr_b && cudaMemcpyAsync(t->d_hdr, hdr.data(), hdr_b, cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
-        (sc_b && cudaMemcpyAsync(t->d_scale, sc.data(), sc_b, cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
-        (pool_bytes && cudaMemcpyAsync(t->d_pool, pool, size_t(pool_bytes), cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
-        cudaStreamSynchronize(stream) != cudaSuccess)
+    const size_t rec_b = a.rec.size() * 4, hdr_b = a.hdr.size() * 4, sc_b = a.scale.size() * 4;
+    if (cudaMalloc(&t->d_rec, rec_b ? rec_b : 16) != cudaSuccess ||
+        cudaMalloc(&t->d_hdr, hdr_b ? hdr_b : 16) != cudaSuccess ||
+        cudaMalloc(&t->d_scale, sc_b ? sc_b : 16) != cudaSuccess ||
+        cudaMalloc(&t->d_pool, size_t(a.pool_bytes > 0 ? a.pool_bytes : 16)) != cudaSuccess) {
+        cuda_fail(t);
+        return HTEX_ERR_OUT_OF_MEMORY;
+    }
+    t->device_bytes = htex_asset_device_bytes(a);
+    *out = t;
+    return HTEX_OK;
+}
+
+htex_status htex_asset_allocate_async(const HtexAssetArrays& a, cudaMemPool_t pool, cudaStream_t stream,
+                                      htex_textures** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(nullptr);
+    htex_textures* t = new (std::nothrow) htex_textures;
+    if (!t) return HTEX_ERR_OUT_OF_MEMORY;
+    t->H = a.H;
+    t->E = a.E;
+    t->C = a.C;
+    t->dtype = a.dtype;
+    t->uniform_log2n = a.uniform_log2n;
+    t->uniform_stride = a.uniform_stride;
+    t->pool_bytes = a.pool_bytes;
+    t->max_log2n = a.max_log2n;
+    t->has_scales = is_scaled(a.dtype);
+    t->device = dev;
+    t->free_stream = stream;
+    cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t rec_b = a.rec.size() * 4, hdr_b = a.hdr.size() * 4, sc_b = a.scale.size() * 4;
+    void** bufs[4] = {&t->d_rec, &t->d_hdr, &t->d_scale, &t->d_pool};
+    const size_t sizes[4] = {rec_b ? rec_b : 16, hdr_b ? hdr_b : 16, sc_b ? sc_b : 16,
+                             size_t(a.pool_bytes > 0 ? a.pool_bytes : 16)};
+    for (int k = 0; k < 4; ++k) {
+        if (cudaMallocFromPoolAsync(bufs[k], sizes[k], pool, stream) != cudaSuccess) {
+            cudaGetLastError();
+            htex_textures_destroy(t);
+            return HTEX_ERR_OUT_OF_MEMORY;
+        }
+    }
+    t->device_bytes = htex_asset_device_bytes(a);
+    *out = t;
+    return HTEX_OK;
+}
+
+htex_status htex_asset_copy_async(const HtexAssetArrays& a, const void* pool, htex_textures* t, cudaStream_t stream) {
+    const size_t rec_b = a.rec.size() * 4, hdr_b = a.hdr.size() * 4, sc_b = a.scale.size() * 4;
+    if ((rec_b && cudaMemcpyAsync(t->d_rec, a.rec.data(), rec_b, cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
+        (hdr_b && cudaMemcpyAsync(t->d_hdr, a.hdr.data(), hdr_b, cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
+        (sc_b && cudaMemcpyAsync(t->d_scale, a.scale.data(), sc_b, cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
+        (a.pool_bytes && cudaMemcpyAsync(t->d_pool, pool, size_t(a.pool_bytes), cudaMemcpyHostToDevice, stream) != cudaSuccess)) {
+        cudaGetLastError();
+        return HTEX_ERR_CUDA;
+    }
+    return HTEX_OK;
+}
+
+namespace {
+
+htex_status upload_prepared(const htex_mesh* m, int32_t C, htex_dtype dtype, const int32_t* log2n,
+                            const void* pool, const float* scales, cudaStream_t stream,
+                            htex_textures** out) {
+    HtexAssetArrays a;
+    htex_status st = htex_asset_arrays(m, C, dtype, log2n, scales, &a);
+    if (st != HTEX_OK) return st;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return cuda_fail(nullptr);
+    if (htex_asset_device_bytes(a) + (int64_t(64) << 20) > int64_t(free_b)) return HTEX_ERR_OUT_OF_MEMORY;
+    htex_textures* t = nullptr;
+    st = htex_asset_allocate(a, &t);
+    if (st != HTEX_OK) return st;
+    if (htex_asset_copy_async(a, pool, t, stream) != HTEX_OK || cudaStreamSynchronize(stream) != cudaSuccess)
         return cuda_fail(t);
     *out = t;
     return HTEX_OK;
@@ -535,9 +606,11 @@ extern "C" htex_status htex_textures_write_pool(const htex_textures* t, int64_t 
 extern "C" void htex_textures_destroy(htex_textures* t) {
     if (!t) return;
     htex_host_path_destroy(t->host_path);
-    cudaFree(t->d_rec);
-    cudaFree(t->d_hdr);
-    cudaFree(t->d_scale);
-    cudaFree(t->d_pool);
+    void* bufs[4] = {t->d_rec, t->d_hdr, t->d_scale, t->d_pool};
+    for (void* b : bufs) {
+        if (!b) continue;
+        if (t->free_stream) cudaFreeAsync(b, t->free_stream);
+        else cudaFree(b);
+    }
     delete t;
 }

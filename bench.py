@@ -47,6 +47,7 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cube", action="store_true")
     p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--no-extras", action="store_true", help="skip the precision and backward measurements")
     p.add_argument("--rows", type=int, default=460, help="cylinder rows (460: the asset-scale mesh)")
     return p.parse_args()
 
@@ -390,6 +391,8 @@ def main():
     # the spec streaming case: the closed cube, 16x16 RGBA FP32, 2^24 queries
     cube = None if args.no_cube else cube_stream(hx, torch, stream, args)
     serving = None if args.no_serving else serving_bench(hx, torch)
+    precision = None if args.no_extras else precision_bench(hx, torch, stream)
+    backward = None if args.no_extras else backward_bench(hx, torch, stream)
 
     peak, peak_src = hbm_peak()
     avg_ms = float(np.mean(launch_ms))
@@ -418,6 +421,7 @@ def main():
             "config": workload_config(mesh.H, mesh.E, nq, "bin" if args.bin else "none"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * (1 if not args.bin else 3), "cube_stream": cube, "serving": serving,
+            "precision": precision, "backward": backward,
             "source_hash": source_hash(),
         }), flush=True)
     if dist:
@@ -514,6 +518,87 @@ def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7):
                                "lookups_per_s": float(sizes.sum()) / wall_plain,
                                "back_to_back_lookups_per_s": plain_rate, "all_resident": True}})
     return res
+
+
+def device_queries(torch, H, n, gen, footprint=False):
+    """Uniform queries drawn on the device (h uniform, (u, v) folded-uniform)."""
+    h = torch.randint(0, H, (n,), device="cuda", dtype=torch.int32, generator=gen)
+    uv = torch.rand((n, 2), device="cuda", generator=gen)
+    fold = uv.sum(1) > 1
+    uv[fold] = 1 - uv[fold]
+    f = (torch.exp2(torch.rand(n, device="cuda", generator=gen) * 8 - 8) if footprint
+         else torch.zeros(n, device="cuda"))
+    q = torch.empty((n, 4), dtype=torch.int32, device="cuda")
+    q[:, 0] = h
+    q[:, 1:3] = uv.contiguous().view(torch.int32)
+    q[:, 3] = f.contiguous().view(torch.int32)
+    return q
+
+
+def timed(torch, stream, fn, reps):
+    for _ in range(3):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def precision_bench(hx, torch, stream):
+    """Config-1 cube and 2^24 queries with FP32 / FP16 / BF16 / E4M3 texels."""
+    import htex_synth as syn
+    fs, fv, V, _ = syn.cube()
+    mesh = hx.Mesh(fs, fv, V)
+    log2n = np.full(mesh.E, 4, np.int32)
+    tex32 = syn.texels_f32(log2n, 4, seed=1)
+    n = 1 << 24
+    q = torch.from_numpy(hx.pack_queries(*syn.queries(mesh.H, n, seed=2))).cuda()
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    res = {}
+    for fmt in ("f32", "f16", "bf16", "e4m3"):
+        tex = hx.Textures.upload(mesh, log2n, tex32, 4, fmt, hx.BUILD_MIPS)
+        ms = timed(torch, stream, lambda: hx.lookup(tex, q, out=out, stream=stream), 50)
+        res[fmt] = {"lookups_per_s": n / (ms / 1e3), "ms": ms, "pool_bytes": tex.pool_bytes}
+        tex.close()
+    return res
+
+
+def backward_bench(hx, torch, stream):
+    """Config 4: closed sphere (about 104k halfedges), 32x32 RGB FP32 edge
+    textures, 2M queries: forward and backward throughput, and a 200-step
+    Adam fit (fresh 2M device-drawn queries per step) from zero texels to a
+    smooth target asset."""
+    import htex_synth as syn
+    from paper_2207_05618_gb300 import fit
+    fs, fv, V, _ = syn.uv_sphere()
+    mesh = hx.Mesh(fs, fv, V)
+    log2n = np.full(mesh.E, 5, np.int32)
+    target = hx.Textures.upload(mesh, log2n, syn.texels_smooth(log2n, 3, seed=2), 3, "f32", hx.BUILD_MIPS)
+    tex = hx.Textures.upload(mesh, log2n, np.zeros(mesh.E * 1024 * 3, np.float32), 3, "f32", hx.BUILD_MIPS)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    n = 2_000_000
+    q = device_queries(torch, mesh.H, n, gen)
+    g = torch.randn((n, 3), device="cuda", generator=gen)
+    grad = torch.zeros(tex.pool_elements, dtype=torch.float32, device="cuda")
+    fwd_ms = timed(torch, stream, lambda: hx.lookup(target, q, stream=stream), 50)
+    bwd_ms = timed(torch, stream, lambda: hx.lookup_backward(target, q, g, grad_texels=grad, stream=stream), 50)
+
+    def batches(step):
+        qq = device_queries(torch, mesh.H, n, gen)
+        return qq, hx.lookup(target, qq)
+
+    r = fit.fit(tex, batches, steps=200, lr=0.05)
+    target.close()
+    tex.close()
+    return {"halfedges": mesh.H, "edges": mesh.E, "queries": n,
+            "forward_lookups_per_s": n / (fwd_ms / 1e3), "backward_queries_per_s": n / (bwd_ms / 1e3),
+            "fit": {"steps": r.steps, "initial_loss": r.losses[0], "final_loss": r.losses[-1],
+                    "final_over_initial": r.ratio, "ms_per_step": r.seconds * 1e3 / r.steps,
+                    "loss_every_20": r.losses[::20]}}
 
 
 def cube_stream(hx, torch, stream, args):

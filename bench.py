@@ -54,10 +54,30 @@ def parse_args():
 
 # ----------------------------------------------------------------- workload
 
+def rank_seed(rank: int) -> int:
+    """Each rank draws its own queries (weak scaling: the same count per GPU)."""
+    return 1000 + rank
+
+
+def reduce_max(x: float, dist, device) -> float:
+    """Max over ranks (the slowest rank times the whole job)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * steps * world / (max_ms / 1e3)
+
+
 def asset_inputs(rank: int, nq: int, rows: int = 460):
     import htex_synth as syn
     fs, fv, V, _ = syn.cylinder(rows=rows)
-    return fs, fv, V, syn.queries(int(fs.sum()), nq, seed=1000 + rank, footprint="loguniform")
+    return fs, fv, V, syn.queries(int(fs.sum()), nq, seed=rank_seed(rank), footprint="loguniform")
 
 
 def workload_config(H, E, nq, flags_name):
@@ -352,13 +372,9 @@ def main():
         dist.barrier()
     t1 = time.time()
     sampler.stop()
-    total_ms = starts[0].elapsed_time(ends[-1])
+    total_ms = reduce_max(starts[0].elapsed_time(ends[-1]), dist, "cuda")
     launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = nq * args.steps * world / (total_ms / 1e3)
+    value = job_rate(nq, args.steps, world, total_ms)
     clocks = sampler.summary(t0, t1)
 
     # end to end through the public API: pinned host queries in, host results out
@@ -378,12 +394,8 @@ def main():
             e2e_step()
         e1.record(stream)
         torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
-        if dist:
-            tt = torch.tensor([ems], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
-        e2e = {"value": nq * ksteps * world / (ems / 1e3), "unit": UNIT,
+        ems = reduce_max(e0.elapsed_time(e1), dist, "cuda")
+        e2e = {"value": job_rate(nq, ksteps, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(q_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4),
                "steps": ksteps, "path": "htex_lookup_host: pinned host queries -> device -> lookup -> pinned host "
                                         "results, 2^21-query chunks pipelined over three streams"}

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -32,6 +33,21 @@ struct GlobalSpace {
     __device__ __forceinline__ uint32_t ld4_if(bool p, off_t o) const { return p ? ld4(o) : 0u; }
     __device__ __forceinline__ uint32_t ld2_if(bool p, off_t o) const { return p ? ld2(o) : 0u; }
     __device__ __forceinline__ uint32_t ld1_if(bool p, off_t o) const { return p ? ld1(o) : 0u; }
+    // 4-byte predicated load with an L2 eviction priority: 'keep' marks the
+    // line to be kept (evict_last), else to leave first (evict_first).
+    __device__ __forceinline__ uint32_t ld4_if_l2(bool p, off_t o, bool keep) const {
+        uint32_t r = 0u;
+        asm("{\n\t.reg .pred q, qk, qs;\n\t.reg .b64 pk, ps;\n\t"
+            "setp.ne.u32 q, %2, 0;\n\t"
+            "setp.ne.and.u32 qk, %3, 0, q;\n\t"
+            "setp.eq.and.u32 qs, %3, 0, q;\n\t"
+            "createpolicy.fractional.L2::evict_last.b64 pk, 1.0;\n\t"
+            "createpolicy.fractional.L2::evict_first.b64 ps, 1.0;\n\t"
+            "@qk ld.global.nc.L2::cache_hint.u32 %0, [%1], pk;\n\t"
+            "@qs ld.global.nc.L2::cache_hint.u32 %0, [%1], ps;\n\t}"
+            : "+r"(r) : "l"(base + o), "r"(uint32_t(p)), "r"(uint32_t(keep)));
+        return r;
+    }
 };
 
 // Shared memory: 'base' points into the kernel's dynamic shared buffer (the
@@ -189,8 +205,10 @@ struct Raw {
     uint32_t a = 0u, b = 0u;
 
     template <class S>
-    __device__ __forceinline__ void load_if(const S& s, bool p, typename S::off_t o) {
-        if constexpr (TB == 8) {
+    __device__ __forceinline__ void load_if(const S& s, bool p, typename S::off_t o, bool coarse = false) {
+        if constexpr (TB == 4 && std::is_same<S, GlobalSpace>::value) {
+            a = s.ld4_if_l2(p, o, coarse);   // coarse levels stay in L2 across queries
+        } else if constexpr (TB == 8) {
             const uint2 r = s.ld8_if(p, o);
             a = r.x;
             b = r.y;

@@ -86,10 +86,13 @@ __device__ __forceinline__ void lookup_loop(const Asset<S>& A, const FwdParams& 
 }
 
 constexpr int kGlobalThreads = 256;
+#ifndef HTEX_GLOBAL_MIN_BLOCKS
+#define HTEX_GLOBAL_MIN_BLOCKS 3   // resident blocks per SM the register budget targets
+#endif
 constexpr int kStagedThreads = 384;
 
 template <int DT, int C, bool BINNED>
-__global__ void __launch_bounds__(kGlobalThreads, 3) k_lookup_global(Asset<GlobalSpace> A, FwdParams p) {
+__global__ void __launch_bounds__(kGlobalThreads, HTEX_GLOBAL_MIN_BLOCKS) k_lookup_global(Asset<GlobalSpace> A, FwdParams p) {
     lookup_loop<DT, C, BINNED, true, Raw<DT, C>::PACKED>(A, p);
 }
 

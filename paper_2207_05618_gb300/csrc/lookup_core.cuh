@@ -14,6 +14,11 @@ struct FwdParams {
     const int32_t* idx;   // binned: original index of each sorted query
 };
 
+// Levels of at most 2^kCoarseLog2 texels a side are read with an L2
+// keep hint (about 84 bytes of RGBA8 per texture: L2-resident for assets of
+// hundreds of thousands of textures), finer ones with a leave-first hint.
+constexpr int kCoarseLog2 = 2;
+
 // Coarsest level a fetch reads (its texels are the widest).
 __device__ __forceinline__ int coarsest(const Lod& d) { return d.l1 >= 0 ? d.l1 : d.l0; }
 
@@ -60,10 +65,10 @@ struct Gather {
 
     // slot k: load texel at byte offset o with data weight wd (W += ws done by caller)
     template <int k, class S>
-    __device__ __forceinline__ void tap(const S& pool, typename S::off_t o, float wd) {
+    __device__ __forceinline__ void tap(const S& pool, typename S::off_t o, float wd, bool coarse) {
         if constexpr (DEFER) {
             w[k] = wd;
-            raw[k].load_if(pool, wd != 0.0f, o);
+            raw[k].load_if(pool, wd != 0.0f, o, coarse);
         } else {
             float t[C];
             load_texel_if<DT, C>(pool, wd != 0.0f, o, t);
@@ -91,13 +96,14 @@ __device__ __forceinline__ void own_taps(const Asset<S>& A, const TexRef& t, int
     using off_t = typename S::off_t;
     constexpr int TB = C * Fmt<DT>::ES;
     const OwnPlan q = own_plan<TB>(t.n, l, x, y, wl);
+    const bool coarse = t.n - l <= kCoarseLog2;
     const float sc = Fmt<DT>::SCALED ? t.scale : 1.0f;
     g.W += q.ws;
     const off_t b = off_t(t.off);
-    g.template tap<k0 + 0>(A.pool, b + off_t(q.o[0]), q.w[0] * sc);
-    g.template tap<k0 + 1>(A.pool, b + off_t(q.o[1]), q.w[1] * sc);
-    g.template tap<k0 + 2>(A.pool, b + off_t(q.o[2]), q.w[2] * sc);
-    g.template tap<k0 + 3>(A.pool, b + off_t(q.o[3]), q.w[3] * sc);
+    g.template tap<k0 + 0>(A.pool, b + off_t(q.o[0]), q.w[0] * sc, coarse);
+    g.template tap<k0 + 1>(A.pool, b + off_t(q.o[1]), q.w[1] * sc, coarse);
+    g.template tap<k0 + 2>(A.pool, b + off_t(q.o[2]), q.w[2] * sc, coarse);
+    g.template tap<k0 + 3>(A.pool, b + off_t(q.o[3]), q.w[3] * sc, coarse);
 }
 
 template <int DT, int C, int k0, bool DEFER, class S>
@@ -106,11 +112,12 @@ __device__ __forceinline__ void edge_taps(const Asset<S>& A, const TexRef& t, in
     using off_t = typename S::off_t;
     constexpr int TB = C * Fmt<DT>::ES;
     const EdgePlan e = edge_plan<TB>(t.n, l, dist, along, flip, row, wl);
+    const bool coarse = t.n - l <= kCoarseLog2;
     const float sc = Fmt<DT>::SCALED ? t.scale : 1.0f;
     g.W += e.ws;
     const off_t b = off_t(t.off);
-    g.template tap<k0 + 0>(A.pool, b + off_t(e.o[0]), e.w[0] * sc);
-    g.template tap<k0 + 1>(A.pool, b + off_t(e.o[1]), e.w[1] * sc);
+    g.template tap<k0 + 0>(A.pool, b + off_t(e.o[0]), e.w[0] * sc, coarse);
+    g.template tap<k0 + 1>(A.pool, b + off_t(e.o[1]), e.w[1] * sc, coarse);
 }
 
 // One edge fetch (Next: row, dist u, along v; Prev: column, dist v, along

@@ -266,3 +266,29 @@ def poisson_requests(count, rate, num_assets, lo=1_000, hi=4_000_000, seed=0):
     sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), count)).astype(np.int64)
     assets = rng.integers(0, num_assets, count)
     return arrivals - arrivals[0], sizes, assets
+
+
+# ----------------------------------------------------------------- cameras
+
+def look_at(eye, target, up):
+    """World-to-view matrix (right-handed, looking down -z)."""
+    eye, target, up = (np.asarray(a, np.float64) for a in (eye, target, up))
+    f = target - eye
+    f /= np.linalg.norm(f)
+    s = np.cross(f, up)
+    s /= np.linalg.norm(s)
+    u = np.cross(s, f)
+    m = np.eye(4)
+    m[0, :3], m[1, :3], m[2, :3] = s, u, -f
+    m[:3, 3] = -m[:3, :3] @ eye
+    return m
+
+
+def perspective(fovy_deg, aspect, near, far):
+    """GL-style projection: visible depth z/w in [-1, 1]."""
+    t = 1.0 / np.tan(np.radians(fovy_deg) / 2)
+    m = np.zeros((4, 4))
+    m[0, 0], m[1, 1] = t / aspect, t
+    m[2, 2], m[2, 3] = (far + near) / (near - far), 2 * far * near / (near - far)
+    m[3, 2] = -1.0
+    return m

@@ -276,6 +276,55 @@ htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, in
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);
 
+/* -------------------------------------------------------------- rendering */
+
+/* The step before the lookup in the paper's pipeline (Section 4.4,
+ * "Rendering": one triangle per halfedge is drawn and each fragment samples
+ * the Htex at its (halfedge, barycentrics)), as CUDA kernels. */
+typedef struct htex_geometry htex_geometry;
+
+/* Device geometry of a mesh: its Next/Vert/Face operators, vertex
+ * positions (host [V][3] float, copied) and the normals of the input mesh
+ * (per face its area vector by Newell's formula, per vertex the normalised
+ * sum of its faces' vectors), computed on the host.  Synchronises stream. */
+htex_status htex_geometry_create(const htex_mesh* m, const float* positions, htex_stream stream,
+                                 htex_geometry** out);
+void htex_geometry_destroy(htex_geometry* g);
+
+/* Alg. 1 (Section 3.1) for every halfedge h: out (device [H][3][3] float)
+ * receives v0 = Vert(Next h), v1 = the mean of the vertices of Face(h),
+ * v2 = Vert(h).  Asynchronous. */
+htex_status htex_triangle_vertices(const htex_geometry* g, float* out, htex_stream stream);
+
+/* Render the intrinsic triangulation (every halfedge's Alg. 1 triangle)
+ * into a query per pixel.
+ *   view_proj  host float[16], row-major: clip = view_proj * (x, y, z, 1);
+ *              NDC x right, y up, depth z/w visible in [-1, 1]; pixel
+ *              (x, y), y down, has its centre at (x + 1/2, y + 1/2)
+ *   queries    device [height][width] htex_query (16-byte aligned): the
+ *              nearest triangle whose closed interior contains the pixel
+ *              centre (ties to the smaller halfedge), its perspective-
+ *              correct barycentrics (u weighs Vert(h), v Vert(Next h),
+ *              Section 4.2) and footprint max(|d(u,v)/dx|, |d(u,v)/dy|)
+ *              per pixel; h = -1 (an invalid query) where nothing is seen
+ *   depth      device [height][width] float, nullable: NDC depth (NaN if empty)
+ * Triangles with a vertex at or behind the camera plane (w <= 0) are not
+ * drawn.  Scratch (8 bytes per pixel) comes stream-ordered from a
+ * library-owned pool.  Asynchronous. */
+htex_status htex_rasterize(const htex_geometry* g, const float* view_proj, int32_t width, int32_t height,
+                           htex_query* queries, float* depth, htex_stream stream);
+
+/* Displacement (Section 5.1): for every halfedge triangle the lattice
+ * (u, v) = (i/T, j/T), i + j <= T (k = 0.. in order of i, then j), is
+ * moved along the interpolated normal of the input mesh (vertex normals at
+ * Vert(h) and Vert(Next h), the face normal at the centroid) by scale times
+ * channel 'channel' of the level-0 lookup at (h, u, v).
+ *   t     textures of the same mesh;  tess  T in [1, 64]
+ *   out   device [H][(T+1)(T+2)/2][3] float
+ * Asynchronous; scratch as htex_rasterize. */
+htex_status htex_displace(const htex_geometry* g, const htex_textures* t, int32_t tess, float scale,
+                          int32_t channel, float* out, htex_stream stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* A lookup server: many assets kept resident under a device-memory budget

@@ -16,6 +16,13 @@ Functions and the passages they follow:
                        of what the paper leaves to the graphics API
   lookup               Section 4.4, Alg. 3 with Alg. 2
   lookup_grad          the derivative of Alg. 3, which is linear in the texels
+  triangle_vertices    Alg. 1 (Section 3.1)
+  vertex_normals       normals of the input mesh for displacement (Section 5.1)
+  rasterize            visibility of the intrinsic triangulation through a
+                       pinhole camera, with barycentrics and footprints
+                       (the rendering of Section 4.4, written as a plain
+                       per-pixel nearest-hit search)
+  displace             displaced lattice vertices (Section 5.1)
 
 Every function is pinned by tests in ``tests/test_oracle_*.py`` against the
 Fig. 2 table, hand-derived values, closed forms and invariants.  Parity is
@@ -79,6 +86,8 @@ def _load():
             for name in ("orc_round_f16", "orc_round_bf16", "orc_round_e4m3"):
                 getattr(lib, name).argtypes = [ctypes.c_double]
                 getattr(lib, name).restype = ctypes.c_double
+            lib.orc_triangle_vertices.argtypes = [i32, P, P, P, P]
+            lib.orc_vertex_normals.argtypes = [i32, i32, i32, P, P, P, P, P, P]
             lib.orc_encode.argtypes = [i32, ctypes.c_double]
             lib.orc_encode.restype = ctypes.c_uint32
             lib.orc_decode.argtypes = [i32, ctypes.c_uint32]
@@ -314,3 +323,110 @@ def encode(fmt: str, rounded: float) -> int:
 
 def decode(fmt: str, bits: int) -> float:
     return float(_load().orc_decode(FMT[fmt], int(bits)))
+
+
+# ----------------------------------------------------------- rendering side
+
+def triangle_vertices(mesh: Mesh, positions) -> np.ndarray:
+    """Alg. 1 for every halfedge: [H][3][3] = (v0, v1, v2)."""
+    pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+    tri = np.empty((mesh.H, 3, 3), np.float64)
+    _load().orc_triangle_vertices(mesh.H, _p(mesh.next), _p(mesh.vert), _p(pos), _p(tri))
+    return tri
+
+
+def vertex_normals(mesh: Mesh, positions):
+    pos = np.ascontiguousarray(positions, np.float64).reshape(-1, 3)
+    vn = np.empty((mesh.num_verts, 3), np.float64)
+    fn = np.empty((mesh.num_faces, 3), np.float64)
+    _load().orc_vertex_normals(mesh.H, mesh.num_verts, mesh.num_faces, _p(mesh.next), _p(mesh.vert),
+                               _p(mesh.face), _p(pos), _p(vn), _p(fn))
+    return vn, fn
+
+
+def _project(view_proj, pts):
+    """Homogeneous clip coordinates of points [..., 3] (row-vector convention: clip = M @ [p, 1])."""
+    M = np.asarray(view_proj, np.float64).reshape(4, 4)
+    ph = np.concatenate([pts, np.ones(pts.shape[:-1] + (1,))], -1)
+    return ph @ M.T
+
+
+def rasterize(mesh: Mesh, positions, view_proj, width: int, height: int):
+    """Per pixel centre (x + 1/2, y + 1/2), the intrinsic triangle seen
+    first: the triangle whose interior (barycentrics >= 0) contains the
+    centre with the smallest depth z/w in [-1, 1]; its perspective-correct
+    barycentrics (u on Vert(h), v on Vert(Next h), Section 4.2) and the
+    footprint max(|d(u,v)/dx|, |d(u,v)/dy|) in uv units per pixel, from the
+    same triangle's barycentrics at the centres one pixel right and down.
+    Returns h [H_px, W_px] (-1 where empty), u, v, footprint, depth, and the
+    barycentric margin and depth gap to the runner-up (for deciding which
+    pixels have a unique answer).  Plain loops over pixels, vectorised over
+    triangles: small images only."""
+    tri = triangle_vertices(mesh, positions)           # v0 = Vert(Next h), v1 = centroid, v2 = Vert(h)
+    clip = _project(view_proj, tri)                    # [H][3][4]
+    w = clip[..., 3]
+    ndc = clip[..., :3] / w[..., None]
+    sx = (ndc[..., 0] * 0.5 + 0.5) * width
+    sy = (0.5 - ndc[..., 1] * 0.5) * height
+    hh = np.full((height, width), -1, np.int64)
+    out = {k: np.full((height, width), np.nan) for k in ("u", "v", "f", "depth", "margin", "gap")}
+
+    def bary(px, py):
+        # screen-space barycentrics of (px, py) in every triangle, then perspective-corrected
+        x0, y0, x1, y1, x2, y2 = sx[:, 0], sy[:, 0], sx[:, 1], sy[:, 1], sx[:, 2], sy[:, 2]
+        den = (y1 - y2) * (x0 - x2) + (x2 - x1) * (y0 - y2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            l0 = ((y1 - y2) * (px - x2) + (x2 - x1) * (py - y2)) / den
+            l1 = ((y2 - y0) * (px - x2) + (x0 - x2) * (py - y2)) / den
+        l2 = 1 - l0 - l1
+        lam = np.stack([l0, l1, l2], 1)
+        z = (lam * ndc[..., 2]).sum(1)
+        pw = lam / w
+        pc = pw / pw.sum(1, keepdims=True)
+        # (u, v, w) weigh (v2, v0, v1): u = pc[2], v = pc[0]
+        return lam, z, pc[:, 2], pc[:, 0]
+
+    valid_tri = np.all(w > 0, 1)
+    for y in range(height):
+        for x in range(width):
+            lam, z, u, v = bary(x + 0.5, y + 0.5)
+            inside = valid_tri & np.all(lam >= 0, 1) & (z >= -1) & (z <= 1)
+            idx = np.nonzero(inside)[0]
+            if idx.size == 0:
+                continue
+            order = idx[np.lexsort((idx, z[idx]))]
+            k = order[0]
+            hh[y, x] = k
+            out["u"][y, x], out["v"][y, x], out["depth"][y, x] = u[k], v[k], z[k]
+            out["margin"][y, x] = lam[k].min()
+            out["gap"][y, x] = (z[order[1]] - z[k]) if order.size > 1 else np.inf
+            _, _, ux, vx = bary(x + 1.5, y + 0.5)
+            _, _, uy, vy = bary(x + 0.5, y + 1.5)
+            out["f"][y, x] = max(np.hypot(ux[k] - u[k], vx[k] - v[k]), np.hypot(uy[k] - u[k], vy[k] - v[k]))
+    return hh, out["u"], out["v"], out["f"], out["depth"], out["margin"], out["gap"]
+
+
+def displace(mesh: Mesh, tex: Textures, positions, tess: int, scale: float, channel: int = 0):
+    """Displacement (Section 5.1): for every halfedge triangle the lattice
+    (u, v) = (i/T, j/T), i + j <= T, of the intrinsic triangle, displaced
+    along the interpolated normal (vertex normals at Vert(h) and Vert(Next h),
+    the face normal at the centroid) by scale times the lookup (level 0).
+    Returns [H][K][3] positions, K = (T+1)(T+2)/2, lattice in (i, j) order."""
+    tri = triangle_vertices(mesh, positions)
+    vn, fn = vertex_normals(mesh, positions)
+    ij = [(i, j) for i in range(tess + 1) for j in range(tess + 1 - i)]
+    K = len(ij)
+    u = np.array([i / tess for i, _ in ij])
+    v = np.array([j / tess for _, j in ij])
+    hs = np.repeat(np.arange(mesh.H, dtype=np.int32), K)
+    uu, vv = np.tile(u, mesh.H), np.tile(v, mesh.H)
+    d = lookup(mesh, tex, (hs, uu, vv, np.zeros_like(uu)))[:, channel].reshape(mesh.H, K)
+    wgt = np.stack([u, v, 1 - u - v], 1)                               # weights of v2, v0, v1
+    P = (wgt[None, :, 0, None] * tri[:, None, 2] + wgt[None, :, 1, None] * tri[:, None, 0]
+         + wgt[None, :, 2, None] * tri[:, None, 1])
+    n2 = vn[mesh.vert]                       # at Vert(h)
+    n0 = vn[mesh.vert[mesh.next]]            # at Vert(Next h)
+    n1 = fn[mesh.face]                       # at the centroid
+    N = wgt[None, :, 0, None] * n2[:, None] + wgt[None, :, 1, None] * n0[:, None] + wgt[None, :, 2, None] * n1[:, None]
+    N = N / np.linalg.norm(N, axis=-1, keepdims=True)
+    return P + scale * d[..., None] * N

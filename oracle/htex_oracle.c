@@ -603,3 +603,55 @@ void orc_pack_pool(int32_t E, const int32_t* log2n, const int64_t* toff, const i
         }
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Alg. 1 (Section 3.1): the vertices of the intrinsic triangle of h are
+ * v0 = Vert(Next h), v1 = the mean of the face's vertices (walking the
+ * Next cycle from h), v2 = Vert(h).  Output [H][3][3] doubles.
+ * ---------------------------------------------------------------------- */
+void orc_triangle_vertices(int32_t H, const int32_t* next, const int32_t* vert, const double* pos,
+                           double* tri)
+{
+    for (int32_t h = 0; h < H; ++h) {
+        int32_t nx = next[h];
+        double c[3] = {pos[3 * vert[h] + 0], pos[3 * vert[h] + 1], pos[3 * vert[h] + 2]};
+        int32_t n = 1;
+        for (int32_t g = nx; g != h; g = next[g]) {
+            for (int k = 0; k < 3; ++k) c[k] += pos[3 * vert[g] + k];
+            ++n;
+        }
+        for (int k = 0; k < 3; ++k) {
+            tri[9 * (int64_t)h + 0 + k] = pos[3 * vert[nx] + k];
+            tri[9 * (int64_t)h + 3 + k] = c[k] / n;
+            tri[9 * (int64_t)h + 6 + k] = pos[3 * vert[h] + k];
+        }
+    }
+}
+
+/* Vertex normals for displacement along the input mesh's normals (Section
+ * 5.1, displacement): each face contributes its area vector (Newell's
+ * formula, half the sum of the cross products of consecutive vertices
+ * around the face) to each of its vertices; the vertex normal is the
+ * normalised sum.  Face centroid normal: the face's normalised area
+ * vector.  Outputs [V][3] and [F][3]. */
+void orc_vertex_normals(int32_t H, int32_t V, int32_t F, const int32_t* next, const int32_t* vert,
+                        const int32_t* face, const double* pos, double* vn, double* fn)
+{
+    for (int32_t i = 0; i < 3 * V; ++i) vn[i] = 0.0;
+    for (int32_t i = 0; i < 3 * F; ++i) fn[i] = 0.0;
+    for (int32_t h = 0; h < H; ++h) {
+        const double* a = &pos[3 * vert[h]];
+        const double* b = &pos[3 * vert[next[h]]];
+        double* f = &fn[3 * face[h]];
+        f[0] += 0.5 * (a[1] * b[2] - a[2] * b[1]);
+        f[1] += 0.5 * (a[2] * b[0] - a[0] * b[2]);
+        f[2] += 0.5 * (a[0] * b[1] - a[1] * b[0]);
+    }
+    for (int32_t h = 0; h < H; ++h)
+        for (int k = 0; k < 3; ++k) vn[3 * vert[h] + k] += fn[3 * face[h] + k];
+    for (int32_t i = 0; i < V + F; ++i) {
+        double* x = i < V ? &vn[3 * i] : &fn[3 * (i - V)];
+        double l = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (l > 0) for (int k = 0; k < 3; ++k) x[k] /= l;
+    }
+}

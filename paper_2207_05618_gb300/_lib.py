@@ -58,6 +58,11 @@ _SIGNATURES = {
     "htex_lookup": ([P, P, I64, P, U32, P, P], I32),
     "htex_lookup_backward": ([P, P, I64, P, P, U32, P, P], I32),
     "htex_lookup_host": ([P, P, I64, P, U32, P, P], I32),
+    "htex_geometry_create": ([P, P, P, PP], I32),
+    "htex_geometry_destroy": ([P], None),
+    "htex_triangle_vertices": ([P, P, P], I32),
+    "htex_rasterize": ([P, P, I32, I32, P, P, P], I32),
+    "htex_displace": ([P, P, I32, ctypes.c_float, I32, P, P], I32),
     "htex_server_create": ([P, PP], I32),
     "htex_server_add_asset": ([P, P, I32, I32, P, P, P, P], I32),
     "htex_server_submit": ([P, I32, P, I64, P, P], I32),

@@ -38,11 +38,12 @@ FALLBACK_HBM_GBS = 6800.0
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=500)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--queries", type=int, default=1 << 24)
-    p.add_argument("--bin", action="store_true", help="reorder queries by halfedge first")
+    p.add_argument("--no-bin", action="store_true",
+                   help="filter the queries in their given order (no sort by halfedge range)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cube", action="store_true")
@@ -204,10 +205,15 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self, t0: float, t1: float):
+        """Samples taken during [t0, t1]; when the timed region was shorter
+        than the sampling period, the samples within 0.25 s of it."""
+        window = "timed region"
+        picked = [(ts, line) for ts, line in self.samples if t0 <= ts <= t1 + 0.15]
+        if not picked:
+            window = "within 0.25 s of the timed region"
+            picked = [(ts, line) for ts, line in self.samples if t0 - 0.25 <= ts <= t1 + 0.25]
         sm, mx, reasons = [], [], set()
-        for ts, line in self.samples:
-            if not (t0 <= ts <= t1 + 0.15):
-                continue
+        for ts, line in picked:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -221,7 +227,7 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(mx)) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 # ------------------------------------------------------------ oracle sample
@@ -340,15 +346,31 @@ def main():
     texels = syn.texels_u8(log2n, 4, seed=21)
     tex = hx.Textures.upload(mesh, log2n, texels, 4, "u8", hx.BUILD_MIPS)
     del texels
-    flags = hx.LOOKUP_BIN if args.bin else 0
+    use_bin = not args.no_bin
+    flags = hx.LOOKUP_BIN if use_bin else 0
     q_host = torch.from_numpy(hx.pack_queries(*qs)).pin_memory()
     q = q_host.cuda()
     out = torch.empty((nq, 4), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     bytes_per_lookup = algorithmic_bytes(mesh.halfedges(), 6, qs, 4)
+    if use_bin:
+        sq = torch.empty_like(q)
+        pos = torch.empty(nq, dtype=torch.int32, device="cuda")
+        sout = torch.empty_like(out)
+    sort_chunk = 1 << 23
+    launches_per_step = (2 * -(-nq // sort_chunk) + 2) if use_bin else 1
 
-    def step():
-        hx.lookup(tex, q, out=out, flags=flags, stream=stream)
+    def step(ev=None):
+        # a0 (sort by halfedge range), a1..a6 (the filter kernel), results back in query order
+        if use_bin:
+            hx.sort_queries(tex, q, sq, pos, stream=stream)
+        if ev is not None:
+            ev[0].record(stream)
+        hx.lookup(tex, sq if use_bin else q, out=sout if use_bin else out, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        if use_bin:
+            hx.gather_results(sout, pos, out=out, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -363,9 +385,10 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.time()
+    filt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for k in range(args.steps):
         starts[k].record(stream)
-        step()
+        step(filt[k])
         ends[k].record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -373,7 +396,8 @@ def main():
     t1 = time.time()
     sampler.stop()
     total_ms = reduce_max(starts[0].elapsed_time(ends[-1]), dist, "cuda")
-    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    launch_ms = [a.elapsed_time(b) for a, b in filt]
     value = job_rate(nq, args.steps, world, total_ms)
     clocks = sampler.summary(t0, t1)
 
@@ -383,7 +407,9 @@ def main():
         out_host = torch.empty((nq, 4), dtype=torch.float32).pin_memory()
         def e2e_step():
             # the C-ABI host-buffer call: copies in, lookups, copies out, pipelined in chunks
-            hx.lookup_host(tex, q_host, out=out_host, flags=flags, stream=stream)
+            # (queries in their given order: the copies bound this call, and sorting the
+            # 2^21-query chunks of three concurrent streams costs more than it saves)
+            hx.lookup_host(tex, q_host, out=out_host, stream=stream)
         for _ in range(3):
             e2e_step()
         torch.cuda.synchronize()
@@ -398,7 +424,8 @@ def main():
         e2e = {"value": job_rate(nq, ksteps, world, ems), "unit": UNIT,
                "h2d_bytes_per_step": int(q_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4),
                "steps": ksteps, "path": "htex_lookup_host: pinned host queries -> device -> lookup -> pinned host "
-                                        "results, 2^21-query chunks pipelined over three streams"}
+                                        "results, 2^21-query chunks pipelined over three streams, queries in "
+                                        "their given order"}
 
     # the spec streaming case: the closed cube, 16x16 RGBA FP32, 2^24 queries
     cube = None if args.no_cube else cube_stream(hx, torch, stream, args)
@@ -409,6 +436,7 @@ def main():
 
     peak, peak_src = hbm_peak()
     avg_ms = float(np.mean(launch_ms))
+    stages = {"filter_ms": avg_ms, "sort_and_gather_ms": float(np.mean(step_ms)) - avg_ms}
     achieved = bytes_per_lookup * nq / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic("lookup"), "peak_source": peak_src,
@@ -431,9 +459,11 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(mesh.H, mesh.E, nq, "bin" if args.bin else "none"),
+            "config": workload_config(mesh.H, mesh.E, nq, "sorted by halfedge range (htex_queries_sort, "
+                                      "htex_lookup, htex_results_gather)" if use_bin else "none"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps * (1 if not args.bin else 3), "cube_stream": cube, "serving": serving,
+            "gpu_launches": args.steps * launches_per_step, "step_ms_stages": stages,
+            "cube_stream": cube, "serving": serving,
             "precision": precision, "backward": backward, "frame": frame,
             "source_hash": source_hash(),
         }), flush=True)

@@ -69,7 +69,7 @@ typedef enum { HTEX_F32 = 0, HTEX_U8 = 1, HTEX_F16 = 2, HTEX_BF16 = 3, HTEX_E4M3
 #define HTEX_LEVELS_GIVEN    8u  /* the caller supplies every level, not only level 0        */
 
 /* Lookup flags (htex_lookup / _backward). */
-#define HTEX_LOOKUP_BIN      1u  /* reorder queries by halfedge before filtering (scratch)    */
+#define HTEX_LOOKUP_BIN      1u  /* sort queries by halfedge range before filtering (scratch) */
 #define HTEX_LOOKUP_GLOBAL   2u  /* never stage textures in shared memory                     */
 
 /* One query: 16 bytes, 16-byte aligned in device memory.
@@ -229,10 +229,15 @@ void htex_textures_destroy(htex_textures* t);
 /* Filtered lookups (Section 4.4, Alg. 3 with Alg. 2), n queries.
  *   q         device [n] htex_query (16-byte aligned)
  *   out       device [n][channels] float (16-byte aligned when channels = 4)
- *   flags     HTEX_LOOKUP_BIN: counting-sort the queries by halfedge first
- *             (needs scratch: allocated stream-ordered on 'stream' and
- *             released there); HTEX_LOOKUP_GLOBAL: never stage the pool in
- *             shared memory (by default a pool of at most 96 KiB is staged)
+ *   flags     HTEX_LOOKUP_BIN: when the pool exceeds 64 MiB, counting-sort
+ *             the queries into ranges of consecutive halfedges first, in
+ *             chunks of 2^23 queries, filter them in that order and gather
+ *             the results back into query order (same results, bit for bit;
+ *             scratch of 20 + 4 * channels bytes per chunk query,
+ *             allocated stream-ordered on 'stream' from a library-owned
+ *             pool and released there; HTEX_ERR_OUT_OF_MEMORY when it cannot
+ *             be had); HTEX_LOOKUP_GLOBAL: never stage the pool in shared
+ *             memory (by default a pool of at most 96 KiB is staged)
  *   d_status  device int32, nullable: incremented once per invalid query
  * For each query: own = quad of Edge(h) at Alg. 2 (h, (u, v)), then the
  * quads of Next(h) at (v, -u) and of Prev(h) at (-v, u); each fetch is a
@@ -243,6 +248,39 @@ void htex_textures_destroy(htex_textures* t);
  * in FP32.  n = 0 is valid and launches nothing.  Asynchronous. */
 htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,
                         uint32_t flags, htex_stream stream, int32_t* d_status);
+
+/* The two halves of HTEX_LOOKUP_BIN as calls of their own, for callers
+ * that filter one sorted batch more than once (several texture sets on
+ * one mesh) or time the filter on its own.  The paper has no counterpart:
+ * query order does not change any result (each query is filtered on its
+ * own, Section 4.4, Alg. 3), only which texels share L2 at a time.
+ *
+ * htex_queries_sort: counting-sorts the queries, within consecutive chunks
+ * of 2^23, into ranges of consecutive halfedges (at most 128 ranges of
+ * 2^s halfedges, the ranges in ascending order, invalid queries last in
+ * their chunk; the order inside a range is unspecified and may differ
+ * from call to call).
+ *   q        device [n] htex_query, 16-byte aligned, n <= 2^31 - 1
+ *   sorted   device [n] htex_query, 16-byte aligned, must not overlap q:
+ *            the queries in sorted order, each unchanged
+ *   pos      device [n] int32: pos[i] = index in 'sorted' of query i
+ * Only t's halfedge count is used.  Needs a few KiB of scratch, allocated
+ * stream-ordered from a library-owned pool (HTEX_ERR_OUT_OF_MEMORY when it
+ * cannot be had).  Asynchronous on 'stream'. */
+htex_status htex_queries_sort(const htex_textures* t, const htex_query* q, int64_t n, htex_query* sorted,
+                              int32_t* pos, htex_stream stream);
+
+/* htex_results_gather: out[i][c] = sorted_out[pos[i]][c] for i < n,
+ * c < channels: the results of htex_lookup on htex_queries_sort's sorted
+ * copy, back in query order.  A pos[i] outside [0, n) gives NaN in every
+ * channel of out[i] and reads nothing.
+ *   sorted_out, out  device float [n][channels], channels 1..4, aligned
+ *                    to 16 bytes (channels 4), 8 (2) or 4 (1, 3); must not
+ *                    overlap
+ *   pos              device int32 [n]
+ * Runs on the current device.  Asynchronous on 'stream'. */
+htex_status htex_results_gather(const float* sorted_out, const int32_t* pos, int64_t n, int32_t channels,
+                                float* out, htex_stream stream);
 
 /* htex_lookup on host buffers (the end-to-end path for callers whose
  * queries and results live in host memory).

@@ -17,7 +17,8 @@ import numpy as np
 from ._lib import (BUILD_MIPS, DTYPES, ELEM_SIZE, FIX_CORNERS, LEVELS_GIVEN, LOOKUP_BIN,
                    LOOKUP_GLOBAL, MIRROR_BOUNDARY, HtexError, check, load)
 
-__all__ = ["Mesh", "Textures", "lookup", "lookup_host", "lookup_backward", "pack_queries", "HtexLookup",
+__all__ = ["Mesh", "Textures", "lookup", "lookup_host", "lookup_backward", "sort_queries", "gather_results",
+           "pack_queries", "HtexLookup",
            "HtexError", "BUILD_MIPS", "MIRROR_BOUNDARY", "FIX_CORNERS", "LEVELS_GIVEN",
            "LOOKUP_BIN", "LOOKUP_GLOBAL"]
 
@@ -226,6 +227,45 @@ def lookup(tex: Textures, queries, out=None, flags: int = 0, stream=None, status
     st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
     check(tex._lib.htex_lookup(tex._h, ctypes.c_void_p(queries.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
                                int(flags), _stream(stream), st), "htex_lookup")
+    return out
+
+
+def sort_queries(tex: Textures, queries, sorted_queries=None, pos=None, stream=None):
+    """htex_queries_sort: queries int32 CUDA tensor [n, 4] -> (the queries
+    sorted by halfedge range, int32 [n, 4]; pos int32 [n], where each query went)."""
+    import torch
+    _check_tensor(queries, "queries", torch.int32, 4)
+    n = queries.shape[0]
+    if sorted_queries is None:
+        sorted_queries = torch.empty_like(queries)
+    else:
+        _check_tensor(sorted_queries, "sorted_queries", torch.int32, 4)
+    if pos is None:
+        pos = torch.empty(n, dtype=torch.int32, device=queries.device)
+    if not (pos.is_cuda and pos.dtype == torch.int32 and pos.is_contiguous() and pos.numel() == n):
+        raise ValueError("pos must be a contiguous CUDA int32 tensor of n elements")
+    check(tex._lib.htex_queries_sort(tex._h, ctypes.c_void_p(queries.data_ptr()), n,
+                                     ctypes.c_void_p(sorted_queries.data_ptr()), ctypes.c_void_p(pos.data_ptr()),
+                                     _stream(stream)), "htex_queries_sort")
+    return sorted_queries, pos
+
+
+def gather_results(sorted_out, pos, out=None, stream=None):
+    """htex_results_gather: float32 CUDA [n, channels] in sorted order -> query order."""
+    import torch
+    if not isinstance(sorted_out, torch.Tensor) or sorted_out.dim() != 2:
+        raise ValueError("sorted_out must be a float32 CUDA tensor [n, channels]")
+    n, c = sorted_out.shape
+    _check_tensor(sorted_out, "sorted_out", torch.float32, c)
+    if not (pos.is_cuda and pos.dtype == torch.int32 and pos.is_contiguous() and pos.numel() == n):
+        raise ValueError("pos must be a contiguous CUDA int32 tensor of n elements")
+    if out is None:
+        out = torch.empty_like(sorted_out)
+    else:
+        _check_tensor(out, "out", torch.float32, c)
+    lib = load()
+    check(lib.htex_results_gather(ctypes.c_void_p(sorted_out.data_ptr()), ctypes.c_void_p(pos.data_ptr()), n, c,
+                                  ctypes.c_void_p(out.data_ptr()), _stream(stream)), "htex_results_gather")
     return out
 
 

@@ -10,10 +10,15 @@
 // pool staged in shared memory (small assets, many queries) or gathered
 // through the read-only cache from global memory.
 //
-// Binning (HTEX_LOOKUP_BIN): a counting sort of the queries by halfedge
-// range (buckets of 2^shift consecutive halfedges, sized so the textures a
-// bucket touches fit in L2), so that queries sharing textures run close
-// together in time and their texel sectors are read from DRAM once.
+// Binning (HTEX_LOOKUP_BIN), for pools well beyond L2: the queries are
+// counting-sorted into 128 ranges of consecutive halfedges, in chunks of
+// 2^23 queries, before filtering.  The filter kernel then works through
+// one range of the asset at a time, so that a texel sector fetched for one
+// query is still in L2 when the queries next to it in the range need it;
+// the ranges' order matters, the order inside a range does not.  The
+// results are filtered into a sorted copy and gathered back into query
+// order.  The allocation-free variant sorts the whole batch at once into
+// ranges sized by texel bytes and stores results through the indices.
 #include <algorithm>
 #include <mutex>
 
@@ -231,11 +236,168 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const htex_query* q
     }
 }
 
+// ------------------------------------------ chunk-local sort (HTEX_LOOKUP_BIN)
+//
+// One chunk of m queries at a time: a bucket histogram, then per tile of
+// kSortTile queries a local counting sort in shared memory, so that every
+// bucket's run of the tile is written to the sorted copy as one contiguous
+// piece (whole sectors, not scattered 16-byte pieces), and each query's
+// sorted position is recorded in query order.  The lookup then filters the
+// sorted copy with coalesced result stores, and the gather puts every
+// result back in query order through the recorded positions.
+
+constexpr int kSortThreads = 256;
+constexpr int kSortPer = 8;
+constexpr int kSortTile = kSortThreads * kSortPer;
+constexpr int kSortMaxBuckets = 512 + 2;   // keeps the scatter's static shared memory under 48 KiB
+
+__global__ void __launch_bounds__(kSortThreads) k_chunk_count(const htex_query* q, int64_t m, int32_t H, int shift,
+                                                              uint32_t B, uint32_t* counts) {
+    __shared__ uint32_t hist[kSortMaxBuckets];
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int64_t t0 = int64_t(blockIdx.x) * kSortTile; t0 < m; t0 += int64_t(gridDim.x) * kSortTile) {
+        int32_t h[kSortPer];
+#pragma unroll
+        for (int k = 0; k < kSortPer; ++k) {
+            const int64_t i = t0 + int64_t(k) * kSortThreads + threadIdx.x;
+            h[k] = i < m ? __ldg(reinterpret_cast<const int32_t*>(q + i)) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < kSortPer; ++k)
+            if (t0 + int64_t(k) * kSortThreads + threadIdx.x < m) atomicAdd(&hist[bucket_of(h[k], H, shift, B - 1)], 1u);
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x)
+        if (hist[b]) atomicAdd(&counts[b], hist[b]);
+}
+
+// Exclusive scan of x[0..B) into y (shared memory), each thread a
+// contiguous piece; returns nothing, ends with a barrier.
+__device__ __forceinline__ void block_scan_buckets(const uint32_t* x, uint32_t* y, uint32_t B, uint32_t* warp_tot) {
+    const uint32_t per = (B + kSortThreads - 1) / kSortThreads;
+    const uint32_t lo = min(B, threadIdx.x * per), hi = min(B, lo + per);
+    uint32_t run = 0;
+    for (uint32_t b = lo; b < hi; ++b) run += x[b];
+    uint32_t incl = run;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t prefix = incl - run;
+    for (int w = 0; w < warp; ++w) prefix += warp_tot[w];
+    for (uint32_t b = lo; b < hi; ++b) {
+        const uint32_t c = x[b];
+        y[b] = prefix;
+        prefix += c;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const htex_query* q, int64_t m, int32_t H, int shift,
+                                                                uint32_t B, const uint32_t* counts, uint32_t* taken,
+                                                                htex_query* sq, int32_t* pos, int32_t pos_base) {
+    __shared__ int4 tile[kSortTile];
+    __shared__ uint16_t tile_bucket[kSortTile];
+    __shared__ uint32_t start[kSortMaxBuckets];    // first sorted position of each bucket
+    __shared__ uint32_t cnt[kSortMaxBuckets];      // the tile's bucket sizes
+    __shared__ uint32_t loff[kSortMaxBuckets];     // the tile's local bucket offsets
+    __shared__ uint32_t gbase[kSortMaxBuckets];    // where the tile's run of each bucket goes
+    __shared__ uint32_t warp_tot[kSortThreads / 32];
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = counts[b];
+    __syncthreads();
+    block_scan_buckets(cnt, start, B, warp_tot);
+
+    for (int64_t t0 = int64_t(blockIdx.x) * kSortTile; t0 < m; t0 += int64_t(gridDim.x) * kSortTile) {
+        const int tm = int(min(int64_t(kSortTile), m - t0));
+        for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0;
+        __syncthreads();
+        int4 r[kSortPer];
+        uint32_t bk[kSortPer], rank[kSortPer];
+#pragma unroll
+        for (int k = 0; k < kSortPer; ++k) {
+            const int j = k * kSortThreads + threadIdx.x;
+            if (j < tm) r[k] = __ldcs(reinterpret_cast<const int4*>(q + t0) + j);
+        }
+#pragma unroll
+        for (int k = 0; k < kSortPer; ++k) {
+            if (k * kSortThreads + int(threadIdx.x) < tm) {
+                bk[k] = bucket_of(r[k].x, H, shift, B - 1);
+                rank[k] = atomicAdd(&cnt[bk[k]], 1u);
+            }
+        }
+        __syncthreads();
+        block_scan_buckets(cnt, loff, B, warp_tot);
+        for (uint32_t b = threadIdx.x; b < B; b += blockDim.x)
+            if (cnt[b]) gbase[b] = start[b] + atomicAdd(&taken[b], cnt[b]);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kSortPer; ++k) {
+            const int j = k * kSortThreads + threadIdx.x;
+            if (j < tm) {
+                const uint32_t lp = loff[bk[k]] + rank[k];
+                tile[lp] = r[k];
+                tile_bucket[lp] = uint16_t(bk[k]);
+                __stcs(pos + t0 + j, pos_base + int32_t(gbase[bk[k]] + rank[k]));
+            }
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < tm; j += kSortThreads) {
+            const uint32_t b = tile_bucket[j];
+            reinterpret_cast<int4*>(sq)[gbase[b] + (uint32_t(j) - loff[b])] = tile[j];
+        }
+        __syncthreads();
+    }
+}
+
+// Results back in query order: out[i] = sorted_out[pos[i]] (NaN where
+// pos[i] is not in [0, m)).
+template <int C>
+__global__ void k_chunk_gather(const float* sout, const int32_t* pos, int64_t m, float* out) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < m; i0 += 4 * stride) {
+        int64_t p[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p[k] = i0 + k * stride < m ? int64_t(__ldcs(pos + i0 + k * stride)) : 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * stride;
+            if (i >= m) continue;
+            if (uint64_t(p[k]) >= uint64_t(m)) {   // not a position of this batch: NaN, no read
+#pragma unroll
+                for (int c = 0; c < C; ++c) out[i * C + c] = __int_as_float(0x7fc00000);
+                continue;
+            }
+            if constexpr (C == 4) {
+                __stcs(reinterpret_cast<float4*>(out) + i, __ldcg(reinterpret_cast<const float4*>(sout) + p[k]));
+            } else if constexpr (C == 2) {
+                __stcs(reinterpret_cast<float2*>(out) + i, __ldcg(reinterpret_cast<const float2*>(sout) + p[k]));
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) __stcs(out + i * C + c, __ldcg(sout + p[k] * C + c));
+            }
+        }
+    }
+}
+
 }  // namespace htex
 
 using namespace htex;
 
 namespace {
+
+#ifndef HTEX_SORT_CHUNK_LOG2
+#define HTEX_SORT_CHUNK_LOG2 23
+#endif
+#ifndef HTEX_CHUNK_BUCKETS
+#define HTEX_CHUNK_BUCKETS 128
+#endif
+constexpr int64_t kSortChunk = int64_t(1) << HTEX_SORT_CHUNK_LOG2;   // queries per L2-resident chunk
+constexpr int64_t kChunkBuckets = HTEX_CHUNK_BUCKETS;                // halfedge ranges a chunk is sorted into
 
 constexpr uint32_t kMaxStageBytes = 96u * 1024u;
 constexpr int64_t kMinStagedQueries = int64_t(1) << 20;
@@ -338,39 +500,140 @@ int htex_bin_shift(const htex_textures* t) {
     return shift;
 }
 
+namespace {
+
+// Buckets of 2^shift consecutive halfedges, at most kChunkBuckets, plus the
+// bucket of invalid queries.
+struct SortPlan {
+    int shift;
+    uint32_t B;
+};
+
+SortPlan sort_plan(int32_t H) {
+    static_assert(kChunkBuckets + 1 <= kSortMaxBuckets, "bucket arrays too small");
+    SortPlan P{0, 0};
+    while ((int64_t(H) >> P.shift) + 1 > kChunkBuckets) ++P.shift;
+    P.B = uint32_t((int64_t(H) >> P.shift) + 2);
+    return P;
+}
+
+size_t counter_bytes(const SortPlan& P) { return (size_t(2 * P.B) * 4 + 255) & ~size_t(255); }
+
+// Sorts q[0..m) into sq within consecutive chunks of kSortChunk queries;
+// pos[i] = pos_base + where query i went.  counters: counter_bytes(P) of
+// scratch.
+htex_status launch_sort(const htex_textures* t, const SortPlan& P, const htex_query* q, int64_t m,
+                        uint32_t* counters, htex_query* sq, int32_t* pos, int32_t pos_base, cudaStream_t s) {
+    const int64_t blocks = int64_t(t->num_sms) * resident_blocks(k_chunk_scatter, kSortThreads, 0);
+    for (int64_t c0 = 0; c0 < m; c0 += kSortChunk) {
+        const int64_t mc = std::min<int64_t>(kSortChunk, m - c0);
+        const int64_t g = std::min<int64_t>((mc + kSortTile - 1) / kSortTile, blocks);
+        if (cudaMemsetAsync(counters, 0, size_t(2 * P.B) * 4, s) != cudaSuccess) return HTEX_ERR_CUDA;
+        k_chunk_count<<<unsigned(g), kSortThreads, 0, s>>>(q + c0, mc, t->H, P.shift, P.B, counters);
+        k_chunk_scatter<<<unsigned(g), kSortThreads, 0, s>>>(q + c0, mc, t->H, P.shift, P.B, counters,
+                                                             counters + P.B, sq + c0, pos + c0,
+                                                             pos_base + int32_t(c0));
+        if (cudaGetLastError() != cudaSuccess) return HTEX_ERR_CUDA;
+    }
+    return HTEX_OK;
+}
+
+// Gathers the results of a chunk back into query order.  Positions are
+// relative to the sorted chunk.
+htex_status launch_gather(const float* sout, const int32_t* pos, int64_t m, int C, float* out, int num_sms,
+                          cudaStream_t s) {
+    const unsigned g = unsigned(std::max(1, num_sms)) * 8;
+    switch (C) {
+    case 1: k_chunk_gather<1><<<g, 256, 0, s>>>(sout, pos, m, out); break;
+    case 2: k_chunk_gather<2><<<g, 256, 0, s>>>(sout, pos, m, out); break;
+    case 3: k_chunk_gather<3><<<g, 256, 0, s>>>(sout, pos, m, out); break;
+    case 4: k_chunk_gather<4><<<g, 256, 0, s>>>(sout, pos, m, out); break;
+    default: return HTEX_ERR_INVALID_ARG;
+    }
+    return cudaGetLastError() == cudaSuccess ? HTEX_OK : HTEX_ERR_CUDA;
+}
+
+int current_device_sms() {
+    static std::mutex mu;
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> g(mu);
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms[dev] = 0;
+    return sms[dev];
+}
+
+}  // namespace
+
 htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,
                                uint32_t flags, htex_stream stream, int32_t* d_status) {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int shift = (flags & HTEX_LOOKUP_BIN) ? htex_bin_shift(t) : -1;
-    if (shift < 0 || n >= (int64_t(1) << 31)) return launch_fwd_dt<false>(t, FwdParams{q, n, out, d_status, nullptr}, flags, s);
+    if (!(flags & HTEX_LOOKUP_BIN) || htex_bin_shift(t) < 0)
+        return launch_fwd_dt<false>(t, FwdParams{q, n, out, d_status, nullptr}, flags, s);
 
-    const uint32_t B = uint32_t((int64_t(t->H) >> shift) + 2);   // + the bucket of invalid queries
-    const size_t qs_b = size_t(n) * 16, idx_b = size_t(n) * 4, cnt_b = size_t(B) * 4;
+    // one chunk at a time: sort, filter into the sorted copy, gather back
+    const SortPlan P = sort_plan(t->H);
+    const int64_t M = std::min<int64_t>(n, kSortChunk);
+    const size_t cnt_b = counter_bytes(P);
+    const size_t sq_b = size_t(M) * 16, pos_b = (size_t(M) * 4 + 255) & ~size_t(255);
+    const size_t sout_b = size_t(M) * 4 * size_t(t->C);
     cudaMemPool_t pool = scratch_pool(t->device);
     if (!pool) return HTEX_ERR_CUDA;
     void* scratch = nullptr;
-    if (cudaMallocFromPoolAsync(&scratch, qs_b + idx_b + 2 * cnt_b + 64, pool, s) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&scratch, cnt_b + sq_b + pos_b + sout_b, pool, s) != cudaSuccess) {
         cudaGetLastError();
         return HTEX_ERR_OUT_OF_MEMORY;
     }
     uint8_t* base = static_cast<uint8_t*>(scratch);
-    htex_query* qs = reinterpret_cast<htex_query*>(base);
-    int32_t* idx = reinterpret_cast<int32_t*>(base + qs_b);
-    uint32_t* counts = reinterpret_cast<uint32_t*>(base + qs_b + idx_b);
-    uint32_t* taken = counts + B;
+    uint32_t* counters = reinterpret_cast<uint32_t*>(base);
+    htex_query* sq = reinterpret_cast<htex_query*>(base + cnt_b);
+    int32_t* pos = reinterpret_cast<int32_t*>(base + cnt_b + sq_b);
+    float* sout = reinterpret_cast<float*>(base + cnt_b + sq_b + pos_b);
+    const uint32_t fwd_flags = flags & ~uint32_t(HTEX_LOOKUP_BIN);
     htex_status st = HTEX_OK;
-    if (cudaMemsetAsync(counts, 0, 2 * cnt_b, s) != cudaSuccess) st = HTEX_ERR_CUDA;
-    if (st == HTEX_OK) {
-        const int64_t g1 = std::min<int64_t>((n + kBinThreads - 1) / kBinThreads, int64_t(t->num_sms) * 4);
-        k_bin_count<<<unsigned(g1), kBinThreads, 0, s>>>(q, n, t->H, shift, B, counts);
-        const int64_t tile = int64_t(kBinThreads) * kBinPerThread;
-        const int64_t g2 = std::min<int64_t>((n + tile - 1) / tile, int64_t(t->num_sms) * 2);
-        k_bin_scatter<<<unsigned(g2), kBinThreads, 0, s>>>(q, n, t->H, shift, B, counts, taken, qs, idx);
-        if (cudaGetLastError() != cudaSuccess) st = HTEX_ERR_CUDA;
+    for (int64_t c0 = 0; c0 < n && st == HTEX_OK; c0 += M) {
+        const int64_t m = std::min<int64_t>(M, n - c0);
+        st = launch_sort(t, P, q + c0, m, counters, sq, pos, 0, s);
+        if (st == HTEX_OK) st = launch_fwd_dt<false>(t, FwdParams{sq, m, sout, d_status, nullptr}, fwd_flags, s);
+        if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, t->num_sms, s);
     }
-    if (st == HTEX_OK) st = launch_fwd_dt<true>(t, FwdParams{qs, n, out, d_status, idx}, flags, s);
     cudaFreeAsync(scratch, s);
     return st;
+}
+
+extern "C" htex_status htex_queries_sort(const htex_textures* t, const htex_query* q, int64_t n,
+                                         htex_query* sorted, int32_t* pos, htex_stream stream) {
+    if (!t || n < 0 || n > int64_t(INT32_MAX)) return HTEX_ERR_INVALID_ARG;
+    if (n == 0) return HTEX_OK;
+    if (!q || !sorted || !pos) return HTEX_ERR_INVALID_ARG;
+    if (((reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(sorted)) & 15u) != 0 ||
+        (reinterpret_cast<uintptr_t>(pos) & 3u) != 0)
+        return HTEX_ERR_INVALID_ARG;
+    if (cudaSetDevice(t->device) != cudaSuccess) return HTEX_ERR_CUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const SortPlan P = sort_plan(t->H);
+    cudaMemPool_t pool = scratch_pool(t->device);
+    if (!pool) return HTEX_ERR_CUDA;
+    void* counters = nullptr;
+    if (cudaMallocFromPoolAsync(&counters, counter_bytes(P), pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return HTEX_ERR_OUT_OF_MEMORY;
+    }
+    const htex_status st = launch_sort(t, P, q, n, static_cast<uint32_t*>(counters), sorted, pos, 0, s);
+    cudaFreeAsync(counters, s);
+    return st;
+}
+
+extern "C" htex_status htex_results_gather(const float* sorted_out, const int32_t* pos, int64_t n, int32_t channels,
+                                           float* out, htex_stream stream) {
+    if (n < 0 || n > int64_t(INT32_MAX) || channels < 1 || channels > 4) return HTEX_ERR_INVALID_ARG;
+    if (n == 0) return HTEX_OK;
+    if (!sorted_out || !pos || !out) return HTEX_ERR_INVALID_ARG;
+    const uintptr_t align = channels == 4 ? 16u : (channels == 2 ? 8u : 4u);
+    if (((reinterpret_cast<uintptr_t>(sorted_out) | reinterpret_cast<uintptr_t>(out)) & (align - 1)) != 0 ||
+        (reinterpret_cast<uintptr_t>(pos) & 3u) != 0)
+        return HTEX_ERR_INVALID_ARG;
+    return launch_gather(sorted_out, pos, n, channels, out, current_device_sms(), reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,

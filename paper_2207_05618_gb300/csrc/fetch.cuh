@@ -33,22 +33,31 @@ struct GlobalSpace {
     __device__ __forceinline__ uint32_t ld4_if(bool p, off_t o) const { return p ? ld4(o) : 0u; }
     __device__ __forceinline__ uint32_t ld2_if(bool p, off_t o) const { return p ? ld2(o) : 0u; }
     __device__ __forceinline__ uint32_t ld1_if(bool p, off_t o) const { return p ? ld1(o) : 0u; }
-    // 4-byte predicated load with an L2 eviction priority: 'keep' marks the
-    // line to be kept (evict_last), else to leave first (evict_first).
-    __device__ __forceinline__ uint32_t ld4_if_l2(bool p, off_t o, bool keep) const {
+    // 4-byte predicated load with an L2 eviction policy (l2_keep_policy or
+    // l2_leave_policy).
+    __device__ __forceinline__ uint32_t ld4_if_pol(bool p, off_t o, uint64_t pol) const {
         uint32_t r = 0u;
-        asm("{\n\t.reg .pred q, qk, qs;\n\t.reg .b64 pk, ps;\n\t"
+        asm("{\n\t.reg .pred q;\n\t"
             "setp.ne.u32 q, %2, 0;\n\t"
-            "setp.ne.and.u32 qk, %3, 0, q;\n\t"
-            "setp.eq.and.u32 qs, %3, 0, q;\n\t"
-            "createpolicy.fractional.L2::evict_last.b64 pk, 1.0;\n\t"
-            "createpolicy.fractional.L2::evict_first.b64 ps, 1.0;\n\t"
-            "@qk ld.global.nc.L2::cache_hint.u32 %0, [%1], pk;\n\t"
-            "@qs ld.global.nc.L2::cache_hint.u32 %0, [%1], ps;\n\t}"
-            : "+r"(r) : "l"(base + o), "r"(uint32_t(p)), "r"(uint32_t(keep)));
+            "@q ld.global.nc.L2::cache_hint.u32 %0, [%1], %3;\n\t}"
+            : "+r"(r) : "l"(base + o), "r"(uint32_t(p)), "l"(pol));
         return r;
     }
 };
+
+// L2 eviction policies: lines to keep (evict_last) and lines to leave first
+// (evict_first).  The asm has no side effects, so the compiler creates each
+// policy once and reuses it.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t l2_leave_policy() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
 
 // Shared memory: 'base' points into the kernel's dynamic shared buffer (the
 // compiler sees where it comes from and emits shared-window loads); offsets
@@ -72,14 +81,19 @@ struct SharedSpace {
 
 // ---------------------------------------------------------------- decoding
 
+// ES: bytes per channel; SCALED: decoded codes are multiplied by the
+// texture's scale; UNIT: constant factor of every decoded code (applied to
+// the tap weights).
 template <int DT> struct Fmt;
-template <> struct Fmt<HTEX_F32> { static constexpr int ES = 4; static constexpr bool SCALED = false; };
-template <> struct Fmt<HTEX_U8> { static constexpr int ES = 1; static constexpr bool SCALED = false; };
-template <> struct Fmt<HTEX_F16> { static constexpr int ES = 2; static constexpr bool SCALED = true; };
-template <> struct Fmt<HTEX_BF16> { static constexpr int ES = 2; static constexpr bool SCALED = true; };
-template <> struct Fmt<HTEX_E4M3> { static constexpr int ES = 1; static constexpr bool SCALED = true; };
+template <> struct Fmt<HTEX_F32> { static constexpr int ES = 4; static constexpr bool SCALED = false; static constexpr float UNIT = 1.0f; };
+template <> struct Fmt<HTEX_U8> { static constexpr int ES = 1; static constexpr bool SCALED = false; static constexpr float UNIT = 1.0f / 255.0f; };
+template <> struct Fmt<HTEX_F16> { static constexpr int ES = 2; static constexpr bool SCALED = true; static constexpr float UNIT = 1.0f; };
+template <> struct Fmt<HTEX_BF16> { static constexpr int ES = 2; static constexpr bool SCALED = true; static constexpr float UNIT = 1.0f; };
+template <> struct Fmt<HTEX_E4M3> { static constexpr int ES = 1; static constexpr bool SCALED = true; static constexpr float UNIT = 1.0f; };
 
-__device__ __forceinline__ float dec_u8(uint32_t b) { return float(b) * (1.0f / 255.0f); }
+// RGBA8 UNORM: the code b stands for b / 255; the lookup kernels apply the
+// 1/255 to the tap weight (Fmt<HTEX_U8>::UNIT) rather than to each channel.
+__device__ __forceinline__ float dec_u8(uint32_t b) { return float(b); }
 __device__ __forceinline__ float dec_f16(uint32_t b) { return __half2float(__ushort_as_half((unsigned short)b)); }
 __device__ __forceinline__ float dec_bf16(uint32_t b) { return __uint_as_float(b << 16); }
 __device__ __forceinline__ float dec_e4m3(uint32_t b) {
@@ -205,9 +219,9 @@ struct Raw {
     uint32_t a = 0u, b = 0u;
 
     template <class S>
-    __device__ __forceinline__ void load_if(const S& s, bool p, typename S::off_t o, bool coarse = false) {
+    __device__ __forceinline__ void load_if(const S& s, bool p, typename S::off_t o, uint64_t pol) {
         if constexpr (TB == 4 && std::is_same<S, GlobalSpace>::value) {
-            a = s.ld4_if_l2(p, o, coarse);   // coarse levels stay in L2 across queries
+            a = s.ld4_if_pol(p, o, pol);   // coarse levels stay in L2 across queries
         } else if constexpr (TB == 8) {
             const uint2 r = s.ld8_if(p, o);
             a = r.x;
@@ -341,6 +355,23 @@ __device__ __forceinline__ Taps1 taps1(float p, int N) {
     return t;
 }
 
+// The same two taps for the forward fetches: the first index i = floor(s)
+// unclamped (in [-1, N - 1]; the second tap is i + 1) and the same weights.
+// A tap outside [0, N) has weight exactly zero and is never loaded, so the
+// offsets can be formed from i without clamping.
+struct TapsU {
+    int i;
+    float w0, w1;
+};
+
+__device__ __forceinline__ TapsU taps_u(float p, int N) {
+    const float s = fmaf(p, float(N), -0.5f);
+    const float fi = floorf(s);
+    const float a = s - fi;
+    const int i = int(fi);
+    return TapsU{i, i >= 0 ? 1.0f - a : 0.0f, i + 1 < N ? a : 0.0f};
+}
+
 // Alg. 3's three fetches, after the query is clamped onto its triangle
 // (u, v >= 0, u + v <= 1):
 //   own    quad of h at (u, v) or (1 - u, 1 - v): inside [0, 1]^2, a 2x2 tap
@@ -359,12 +390,14 @@ __device__ __forceinline__ float across_weight(float dist, int N) {
     return fmaf(-dist, float(N), 0.5f);
 }
 
-// Taps of the own fetch at one level: byte offsets from the texture start
-// of (i0, j0), (i1, j0), (i0, j1), (i1, j1), their weights (level weight
-// included) and the level's share of the normalisation sum.  A tap of
-// weight zero is never loaded.
+// Taps of the own fetch at one level: the byte offset o (from the texture
+// start) of tap (i, j), the others at o + TB, o + row and o + row + TB;
+// their weights (level weight included) in the order (i, j), (i + 1, j),
+// (i, j + 1), (i + 1, j + 1), and the level's share of the normalisation
+// sum.  A tap of weight zero is never loaded (its offset may lie outside
+// the texture).
 struct OwnPlan {
-    uint32_t o[4];
+    int32_t o, row;
     float w[4];
     float ws;
 };
@@ -372,14 +405,10 @@ struct OwnPlan {
 template <int TB>
 __device__ __forceinline__ OwnPlan own_plan(int n, int l, float x, float y, float wl) {
     const int N = 1 << (n - l);
-    const Taps1 tx = taps1(x, N), ty = taps1(y, N);
-    const uint32_t lvl = level_texels(n, l) * uint32_t(TB);
-    const uint32_t r0 = lvl + uint32_t(ty.i0 * N) * TB, r1 = lvl + uint32_t(ty.i1 * N) * TB;
+    const TapsU tx = taps_u(x, N), ty = taps_u(y, N);
     OwnPlan q;
-    q.o[0] = r0 + uint32_t(tx.i0) * TB;
-    q.o[1] = r0 + uint32_t(tx.i1) * TB;
-    q.o[2] = r1 + uint32_t(tx.i0) * TB;
-    q.o[3] = r1 + uint32_t(tx.i1) * TB;
+    q.row = N * TB;
+    q.o = int32_t(level_texels(n, l)) * TB + (ty.i * N + tx.i) * TB;
     const float y0 = ty.w0 * wl, y1 = ty.w1 * wl;
     q.w[0] = y0 * tx.w0;
     q.w[1] = y0 * tx.w1;
@@ -390,10 +419,11 @@ __device__ __forceinline__ OwnPlan own_plan(int n, int l, float x, float y, floa
 }
 
 // Taps of a Next (row = true) or Prev fetch at one level: the two texels of
-// the row or column on the shared side, weights including the across weight
-// and the level weight (all zero when the query lies too far away).
+// the row or column on the shared side, at o and o + step, with weights
+// including the across weight and the level weight (all zero when the
+// query lies too far away).
 struct EdgePlan {
-    uint32_t o[2];
+    int32_t o, step;
     float w[2];
     float ws;
 };
@@ -404,14 +434,13 @@ __device__ __forceinline__ EdgePlan edge_plan(int n, int l, float dist, float al
     const int N = 1 << (n - l);
     const float wa = across_weight(dist, N);
     const float waw = wa > 0.0f ? wa * wl : 0.0f;
-    const Taps1 ta = taps1(flip ? 1.0f - along : along, N);
+    const TapsU ta = taps_u(flip ? 1.0f - along : along, N);
     const int k = flip ? N - 1 : 0;
-    const uint32_t lvl = level_texels(n, l) * uint32_t(TB);
     // texel (i, k) of the row or (k, i) of the column, row-major j * N + i
-    const uint32_t stride_i = row ? 1u : uint32_t(N), fixed = row ? uint32_t(k * N) : uint32_t(k);
+    const int stride_i = row ? 1 : N, fixed = row ? k * N : k;
     EdgePlan e;
-    e.o[0] = lvl + (fixed + uint32_t(ta.i0) * stride_i) * TB;
-    e.o[1] = lvl + (fixed + uint32_t(ta.i1) * stride_i) * TB;
+    e.step = stride_i * TB;
+    e.o = int32_t(level_texels(n, l)) * TB + (fixed + ta.i * stride_i) * TB;
     e.w[0] = ta.w0 * waw;
     e.w[1] = ta.w1 * waw;
     e.ws = waw * (ta.w0 + ta.w1);
@@ -463,12 +492,9 @@ __device__ __forceinline__ void prefetch_query(const htex_query* q, int64_t i) {
 // Streaming 16-byte query load: bypasses L1 and is marked first to leave L2.
 __device__ __forceinline__ int4 ld_query(const htex_query* q, int64_t i) {
     int4 r;
-    asm volatile(
-        "{\n\t.reg .b64 pol;\n\t"
-        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
-        "ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], pol;\n\t}"
-        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(reinterpret_cast<const int4*>(q) + i));
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(reinterpret_cast<const int4*>(q) + i), "l"(l2_leave_policy()));
     return r;
 }
 

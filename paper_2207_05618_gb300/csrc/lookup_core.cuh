@@ -63,15 +63,16 @@ struct Gather {
         for (int k = 0; k < (DEFER ? K : 1); ++k) w[k] = 0.0f;
     }
 
-    // slot k: load texel at byte offset o with data weight wd (W += ws done by caller)
+    // slot k: when 'on', load the texel at byte offset o; data weight wd
+    // (W += ws done by the caller)
     template <int k, class S>
-    __device__ __forceinline__ void tap(const S& pool, typename S::off_t o, float wd, bool coarse) {
+    __device__ __forceinline__ void tap(const S& pool, typename S::off_t o, bool on, float wd, uint64_t pol) {
         if constexpr (DEFER) {
             w[k] = wd;
-            raw[k].load_if(pool, wd != 0.0f, o, coarse);
+            raw[k].load_if(pool, on, o, pol);
         } else {
             float t[C];
-            load_texel_if<DT, C>(pool, wd != 0.0f, o, t);
+            load_texel_if<DT, C>(pool, on, o, t);
 #pragma unroll
             for (int c = 0; c < C; ++c) acc[c] = fmaf(wd, t[c], acc[c]);
         }
@@ -90,20 +91,29 @@ struct Gather {
     }
 };
 
+// Data weight factor of a texture's decoded codes: its scale (scaled
+// formats) times the format's unit (1/255 for RGBA8).
+template <int DT>
+__device__ __forceinline__ float code_factor(const TexRef& t) {
+    return (Fmt<DT>::SCALED ? t.scale : 1.0f) * Fmt<DT>::UNIT;
+}
+
+// Taps are loaded only where their weight (before the code factor) is
+// nonzero: exactly the taps inside the texture.
 template <int DT, int C, int k0, bool DEFER, class S>
 __device__ __forceinline__ void own_taps(const Asset<S>& A, const TexRef& t, int l, float x, float y, float wl,
                                          Gather<DT, C, DEFER>& g) {
     using off_t = typename S::off_t;
     constexpr int TB = C * Fmt<DT>::ES;
     const OwnPlan q = own_plan<TB>(t.n, l, x, y, wl);
-    const bool coarse = t.n - l <= kCoarseLog2;
-    const float sc = Fmt<DT>::SCALED ? t.scale : 1.0f;
+    const uint64_t pol = t.n - l <= kCoarseLog2 ? l2_keep_policy() : l2_leave_policy();
+    const float sc = code_factor<DT>(t);
     g.W += q.ws;
-    const off_t b = off_t(t.off);
-    g.template tap<k0 + 0>(A.pool, b + off_t(q.o[0]), q.w[0] * sc, coarse);
-    g.template tap<k0 + 1>(A.pool, b + off_t(q.o[1]), q.w[1] * sc, coarse);
-    g.template tap<k0 + 2>(A.pool, b + off_t(q.o[2]), q.w[2] * sc, coarse);
-    g.template tap<k0 + 3>(A.pool, b + off_t(q.o[3]), q.w[3] * sc, coarse);
+    const off_t b = off_t(t.off) + off_t(int64_t(q.o)), r = off_t(q.row);
+    g.template tap<k0 + 0>(A.pool, b, q.w[0] != 0.0f, q.w[0] * sc, pol);
+    g.template tap<k0 + 1>(A.pool, b + TB, q.w[1] != 0.0f, q.w[1] * sc, pol);
+    g.template tap<k0 + 2>(A.pool, b + r, q.w[2] != 0.0f, q.w[2] * sc, pol);
+    g.template tap<k0 + 3>(A.pool, b + r + TB, q.w[3] != 0.0f, q.w[3] * sc, pol);
 }
 
 template <int DT, int C, int k0, bool DEFER, class S>
@@ -112,12 +122,12 @@ __device__ __forceinline__ void edge_taps(const Asset<S>& A, const TexRef& t, in
     using off_t = typename S::off_t;
     constexpr int TB = C * Fmt<DT>::ES;
     const EdgePlan e = edge_plan<TB>(t.n, l, dist, along, flip, row, wl);
-    const bool coarse = t.n - l <= kCoarseLog2;
-    const float sc = Fmt<DT>::SCALED ? t.scale : 1.0f;
+    const uint64_t pol = t.n - l <= kCoarseLog2 ? l2_keep_policy() : l2_leave_policy();
+    const float sc = code_factor<DT>(t);
     g.W += e.ws;
-    const off_t b = off_t(t.off);
-    g.template tap<k0 + 0>(A.pool, b + off_t(e.o[0]), e.w[0] * sc, coarse);
-    g.template tap<k0 + 1>(A.pool, b + off_t(e.o[1]), e.w[1] * sc, coarse);
+    const off_t b = off_t(t.off) + off_t(int64_t(e.o));
+    g.template tap<k0 + 0>(A.pool, b, e.w[0] != 0.0f, e.w[0] * sc, pol);
+    g.template tap<k0 + 1>(A.pool, b + off_t(e.step), e.w[1] != 0.0f, e.w[1] * sc, pol);
 }
 
 // One edge fetch (Next: row, dist u, along v; Prev: column, dist v, along

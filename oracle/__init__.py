@@ -80,6 +80,7 @@ def _load():
             lib.orc_quantize.argtypes = [i32, P, P, i32, i32, P, P, P]
             lib.orc_lookup.argtypes = [i32, P, P, P, P, P, P, P, i32, i64, P, P, P, P, P, P, i32]
             lib.orc_lookup_grad.argtypes = [i32, P, P, P, P, P, P, P, i32, i64, P, P, P, P, P, P]
+            lib.orc_lookup_aniso.argtypes = [i32, P, P, P, P, P, P, P, i32, i64, P, P, P, P, i32, P, i32]
             lib.orc_pool_offsets.argtypes = [i32, P, i32, i32, P]
             lib.orc_pool_offsets.restype = i64
             lib.orc_pack_pool.argtypes = [i32, P, P, P, i32, i32, P, P, P]
@@ -281,6 +282,25 @@ def lookup(mesh: Mesh, tex: Textures, queries, nthreads: int = 1, return_weight:
                        _p(h), _p(u), _p(v), _p(f), _p(out), _p(w) if w is not None else None,
                        int(nthreads))
     return (out, w) if return_weight else out
+
+
+def lookup_aniso(mesh: Mesh, tex: Textures, queries, kmax: int, nthreads: int = 1) -> np.ndarray:
+    """Anisotropic lookups (the reading of Section 5.1's anisotropic filter
+    written out in ``htex_oracle.c``): queries (h, u, v, du/dx, dv/dx, du/dy,
+    dv/dy), the derivatives taken as float32 like the stored query; returns
+    fp64 [n][C]."""
+    h, u, v, dudx, dvdx, dudy, dvdy = queries
+    h = np.ascontiguousarray(h, np.int32)
+    u = np.ascontiguousarray(u, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    d = np.ascontiguousarray(np.stack([dudx, dvdx, dudy, dvdy], 1), np.float32)
+    n = int(h.shape[0])
+    assert u.shape == v.shape == h.shape and d.shape == (n, 4)
+    out = np.empty((n, tex.channels), np.float64)
+    _load().orc_lookup_aniso(mesh.H, _p(mesh.twin), _p(mesh.next), _p(mesh.prev), _p(mesh.edge),
+                             _p(tex.log2n), _p(tex.toff), _p(tex.values), tex.channels, n,
+                             _p(h), _p(u), _p(v), _p(d), int(kmax), _p(out), int(nthreads))
+    return out
 
 
 def lookup_grad(mesh: Mesh, tex: Textures, queries, grad_out) -> np.ndarray:

@@ -562,6 +562,132 @@ void orc_lookup_grad(int32_t H, const int32_t* twin, const int32_t* next, const 
 }
 
 /* ------------------------------------------------------------------------
+ * Anisotropic lookup.  Section 5.1 renders Htex with the GPU's anisotropic
+ * filter applied to each of Alg. 3's three texture fetches; the paper gives
+ * no formula of its own, so this is the reading of it (one sampler applied
+ * to each fetch, one shared normalisation):
+ *   - the footprint is given by the screen derivatives of the barycentrics,
+ *     ax = (du/dx, dv/dx) and ay = (du/dy, dv/dy), in quad-uv units (the
+ *     quad coordinates of every fetch are the barycentrics up to a rotation
+ *     or reflection, so lengths are the same in all three);
+ *   - px2 = |ax|^2, py2 = |ay|^2; the major axis m is ay when py2 > px2,
+ *     else ax; the probe count K is 1 when both are zero, else
+ *     min(ceil(sqrt(max / min)), kmax) (min = 0 gives kmax).  K is an
+ *     integer decided by rounding, so it is computed in FP32 with the same
+ *     operations as the kernel (each product, sum, quotient and square root
+ *     rounded to float);
+ *   - each probe is an isotropic trilinear sample (the level rule of
+ *     'fetch') with footprint Pmax / K, Pmax = sqrt(max);
+ *   - the K probes sit at c + m * s * ((k + 1/2) / K - 1/2), k = 0..K-1,
+ *     around the clamped centre c, with s = min(1, K / Pmax): the probes
+ *     span the major axis, but never more than K quad widths;
+ *   - every probe samples all three fetches of Alg. 3 at its own (u', v'):
+ *     own quad at (u', v'), Next's at (v', -u'), Prev's at (-v', u'), each
+ *     through Alg. 2, full 2x2 taps with a zero border; the result is the
+ *     summed data over the summed normalisation weight (0 / 0 = NaN when
+ *     every tap of every probe falls outside the three quads).
+ * An invalid h, a non-finite u, v or derivative, or an overflowing |ax|^2
+ * or |ay|^2 gives NaN.
+ * ---------------------------------------------------------------------- */
+static int32_t aniso_probes(float dudx, float dvdx, float dudy, float dvdy, int32_t kmax, int* major_y,
+                            double* pmax)
+{
+    volatile float px2 = dudx * dudx;
+    px2 = px2 + (float)(dvdx * dvdx);
+    volatile float py2 = dudy * dudy;
+    py2 = py2 + (float)(dvdy * dvdy);
+    *major_y = py2 > px2;
+    float mx = *major_y ? py2 : px2, mn = *major_y ? px2 : py2;
+    *pmax = sqrt((double)mx);
+    if (mx == 0.0f) return 1;
+    volatile float q = mx / mn;
+    float r = sqrtf(q);
+    if (!(r < (float)kmax)) return kmax;
+    int32_t k = (int32_t)ceilf(r);
+    return k < 1 ? 1 : k;
+}
+
+static void lookup_aniso_one(const orc_asset* A, int32_t h, double u, double v, const float* d, int32_t kmax,
+                             double* out)
+{
+    int32_t C = A->C;
+    int ok = h >= 0 && h < A->H && isfinite(u) && isfinite(v);
+    for (int k = 0; k < 4; ++k) ok = ok && isfinite(d[k]);
+    if (ok) {
+        float px2 = d[0] * d[0], py2 = d[2] * d[2];
+        px2 = px2 + (float)(d[1] * d[1]);
+        py2 = py2 + (float)(d[3] * d[3]);
+        ok = isfinite(px2) && isfinite(py2);
+    }
+    if (!ok) {
+        for (int32_t c = 0; c < C; ++c) out[c] = NAN;
+        return;
+    }
+    clamp_query(&u, &v);
+    int major_y;
+    double pmax;
+    int32_t K = aniso_probes(d[0], d[1], d[2], d[3], kmax, &major_y, &pmax);
+    double mu = major_y ? d[2] : d[0], mv = major_y ? d[3] : d[1];
+    double s = (pmax > (double)K) ? (double)K / pmax : 1.0;
+    double fiso = pmax / (double)K;
+    int32_t hn = A->next[h], hp = A->prev[h];
+    int32_t e[3] = {A->edge[h], A->edge[hn], A->edge[hp]};
+    double acc[16], W = 0.0;
+    for (int32_t c = 0; c < C; ++c) acc[c] = 0.0;
+    for (int32_t k = 0; k < K; ++k) {
+        double t = ((double)k + 0.5) / (double)K - 0.5;
+        double pu = u + mu * s * t, pv = v + mv * s * t;
+        double x[3], y[3];
+        triangle_to_quad_uv(A, h, pu, pv, &x[0], &y[0]);
+        triangle_to_quad_uv(A, hn, pv, -pu, &x[1], &y[1]);
+        triangle_to_quad_uv(A, hp, -pv, pu, &x[2], &y[2]);
+        for (int f = 0; f < 3; ++f) fetch(A, e[f], x[f], y[f], fiso, acc, &W, NULL, NULL, 0.0);
+    }
+    for (int32_t c = 0; c < C; ++c) out[c] = acc[c] / W;
+}
+
+typedef struct {
+    const orc_asset* A;
+    const int32_t* h;
+    const double *u, *v;
+    const float* d;
+    int32_t kmax;
+    double* out;
+    int64_t begin, end;
+} orc_aniso_job;
+
+static void* aniso_job(void* arg)
+{
+    orc_aniso_job* J = (orc_aniso_job*)arg;
+    for (int64_t q = J->begin; q < J->end; ++q)
+        lookup_aniso_one(J->A, J->h[q], J->u[q], J->v[q], J->d + 4 * q, J->kmax, J->out + q * J->A->C);
+    return NULL;
+}
+
+/* Anisotropic lookups of n queries; d holds du/dx, dv/dx, du/dy, dv/dy per
+ * query (float, as stored in the query); kmax >= 1 bounds the probe count. */
+void orc_lookup_aniso(int32_t H, const int32_t* twin, const int32_t* next, const int32_t* prev,
+                      const int32_t* edge, const int32_t* log2n, const int64_t* toff, const double* tex,
+                      int32_t C, int64_t n, const int32_t* qh, const double* qu, const double* qv,
+                      const float* qd, int32_t kmax, double* out, int32_t nthreads)
+{
+    orc_asset A = {H, twin, next, prev, edge, log2n, toff, tex, C};
+    if (kmax < 1) kmax = 1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    orc_aniso_job jobs[256];
+    for (int32_t t = 0; t < nthreads; ++t) {
+        jobs[t].A = &A; jobs[t].h = qh; jobs[t].u = qu; jobs[t].v = qv; jobs[t].d = qd; jobs[t].kmax = kmax;
+        jobs[t].out = out;
+        jobs[t].begin = n * t / nthreads; jobs[t].end = n * (t + 1) / nthreads;
+    }
+    if (nthreads == 1) { aniso_job(&jobs[0]); return; }
+    for (int32_t t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, aniso_job, &jobs[t]);
+    for (int32_t t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+}
+
+/* ------------------------------------------------------------------------
  * Storage-format packer: writes oracle texel values into the documented
  * pool layout so stored pools can be compared byte for byte.  Texture e
  * starts at byte offset poff[e] (each texture padded to a multiple of 16

@@ -433,6 +433,7 @@ def main():
     frame = None if args.no_extras else frame_bench(hx, torch, stream, mesh, tex, positions, args.rows)
     precision = None if args.no_extras else precision_bench(hx, torch, stream)
     backward = None if args.no_extras else backward_bench(hx, torch, stream)
+    aniso = None if args.no_extras else aniso_bench(hx, torch, stream, mesh, tex)
 
     peak, peak_src = hbm_peak()
     avg_ms = float(np.mean(launch_ms))
@@ -464,7 +465,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * launches_per_step, "step_ms_stages": stages,
             "cube_stream": cube, "serving": serving,
-            "precision": precision, "backward": backward, "frame": frame,
+            "precision": precision, "backward": backward, "frame": frame, "aniso": aniso,
             "source_hash": source_hash(),
         }), flush=True)
     if dist:
@@ -630,6 +631,36 @@ def precision_bench(hx, torch, stream):
         res[fmt] = {"lookups_per_s": n / (ms / 1e3), "ms": ms, "pool_bytes": tex.pool_bytes}
         tex.close()
     return res
+
+
+def aniso_bench(hx, torch, stream, mesh, tex, n=1 << 22):
+    """Anisotropic lookups on the asset-scale textures: major axis
+    log-uniform 2^-8..1 quad widths, anisotropy log-uniform 1..16, uniform
+    direction, at most 16 probes."""
+    import htex_synth as syn
+    h, u, v, _ = syn.queries(mesh.H, n, seed=31)
+    rng = np.random.default_rng(32)
+    major = np.exp2(rng.uniform(-8.0, 0.0, n))
+    minor = major / np.exp(rng.uniform(0.0, np.log(16.0), n))
+    th = rng.uniform(0, 2 * np.pi, n)
+    c, s = np.cos(th), np.sin(th)
+    d = [np.float32(x) for x in (major * c, major * s, -minor * s, minor * c)]
+    px2, py2 = d[0] * d[0] + d[1] * d[1], d[2] * d[2] + d[3] * d[3]
+    k = np.minimum(np.ceil(np.sqrt(np.maximum(px2, py2) / np.minimum(px2, py2))), 16)
+    q = torch.from_numpy(hx.pack_queries_aniso(h, u, v, *d)).cuda()
+    out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        hx.lookup_aniso(tex, q, 16, out=out, stream=stream)
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        hx.lookup_aniso(tex, q, 16, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"queries": n, "max_aniso": 16, "mean_probes": float(k.mean()), "ms": ms,
+            "lookups_per_s": n / (ms / 1e3), "probes_per_s": float(k.sum()) / (ms / 1e3)}
 
 
 def backward_bench(hx, torch, stream):

@@ -88,6 +88,18 @@ typedef struct {
     float u, v, footprint;
 } htex_query;
 
+/* One anisotropic query: 32 bytes, 16-byte aligned in device memory.
+ *   h, u, v     as in htex_query
+ *   pad         ignored
+ *   dudx, dvdx  derivatives of (u, v) along screen x (quad-uv units per
+ *               pixel), dudy, dvdy along screen y: the footprint whose
+ *               longer axis the probes of htex_lookup_aniso follow. */
+typedef struct {
+    int32_t h;
+    float u, v, pad;
+    float dudx, dvdx, dudy, dvdy;
+} htex_query_aniso;
+
 typedef struct CUstream_st* htex_stream;
 
 typedef struct htex_mesh htex_mesh;          /* host-side halfedge mesh (opaque)        */
@@ -248,6 +260,30 @@ void htex_textures_destroy(htex_textures* t);
  * in FP32.  n = 0 is valid and launches nothing.  Asynchronous. */
 htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,
                         uint32_t flags, htex_stream stream, int32_t* d_status);
+
+/* Anisotropic filtered lookups, n queries.  Section 5.1 renders Htex with
+ * the GPU's anisotropic filter applied to each of Alg. 3's three fetches;
+ * the paper states no formula, so this is one reading of it:
+ *   px2 = |(dudx, dvdx)|^2, py2 = |(dudy, dvdy)|^2 (float); the major axis
+ *   m is the y derivative when py2 > px2, else the x derivative; the probe
+ *   count K = 1 when both are zero, else min(ceil(sqrt(max / min)),
+ *   max_aniso); each probe is a trilinear sample with footprint Pmax / K
+ *   (Pmax = sqrt(max), the level rule of htex_query); probe k sits at
+ *   (u, v) + m s ((k + 1/2) / K - 1/2) with s = min(1, K / Pmax), and
+ *   samples all three fetches there (own quad at (u', v'), Next's at
+ *   (v', -u'), Prev's at (-v', u'), through Alg. 2, zero border); the result
+ *   is the summed data over the summed normalisation weight.  (u, v) is
+ *   clamped onto the triangle as in htex_lookup before the probes are
+ *   placed.
+ *   q          device [n] htex_query_aniso (16-byte aligned)
+ *   max_aniso  1..16
+ *   out        device [n][channels] float (alignment as htex_lookup)
+ *   d_status   device int32, nullable: incremented once per invalid query
+ *              (h out of range, non-finite u, v or derivative, or an
+ *              overflowing squared length); such a query gives NaN.
+ * FP32 accumulation over at most 24 * max_aniso taps.  Asynchronous. */
+htex_status htex_lookup_aniso(const htex_textures* t, const htex_query_aniso* q, int64_t n, int32_t max_aniso,
+                              float* out, htex_stream stream, int32_t* d_status);
 
 /* The two halves of HTEX_LOOKUP_BIN as calls of their own, for callers
  * that filter one sorted batch more than once (several texture sets on

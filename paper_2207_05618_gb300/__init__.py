@@ -17,8 +17,8 @@ import numpy as np
 from ._lib import (BUILD_MIPS, DTYPES, ELEM_SIZE, FIX_CORNERS, LEVELS_GIVEN, LOOKUP_BIN,
                    LOOKUP_GLOBAL, MIRROR_BOUNDARY, HtexError, check, load)
 
-__all__ = ["Mesh", "Textures", "lookup", "lookup_host", "lookup_backward", "sort_queries", "gather_results",
-           "pack_queries", "HtexLookup",
+__all__ = ["Mesh", "Textures", "lookup", "lookup_host", "lookup_backward", "lookup_aniso", "sort_queries",
+           "gather_results", "pack_queries", "pack_queries_aniso", "HtexLookup",
            "HtexError", "BUILD_MIPS", "MIRROR_BOUNDARY", "FIX_CORNERS", "LEVELS_GIVEN",
            "LOOKUP_BIN", "LOOKUP_GLOBAL"]
 
@@ -227,6 +227,30 @@ def lookup(tex: Textures, queries, out=None, flags: int = 0, stream=None, status
     st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
     check(tex._lib.htex_lookup(tex._h, ctypes.c_void_p(queries.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
                                int(flags), _stream(stream), st), "htex_lookup")
+    return out
+
+
+def pack_queries_aniso(h, u, v, dudx, dvdx, dudy, dvdy) -> np.ndarray:
+    """int32 [n, 8] rows laid out as htex_query_aniso (h, u, v, pad, du/dx,
+    dv/dx, du/dy, dv/dy; the floats bit-cast)."""
+    h = np.ascontiguousarray(h, np.int32)
+    cols = [np.ascontiguousarray(a, np.float32).view(np.int32) for a in (u, v)]
+    d = [np.ascontiguousarray(a, np.float32).view(np.int32) for a in (dudx, dvdx, dudy, dvdy)]
+    return np.ascontiguousarray(np.stack([h, cols[0], cols[1], np.zeros_like(h)] + d, 1))
+
+
+def lookup_aniso(tex: Textures, queries, max_aniso: int = 16, out=None, stream=None, status=None):
+    """htex_lookup_aniso: queries int32 CUDA tensor [n, 8] -> float32 [n, channels]."""
+    import torch
+    _check_tensor(queries, "queries", torch.int32, 8)
+    n = queries.shape[0]
+    if out is None:
+        out = torch.empty((n, tex.channels), dtype=torch.float32, device=queries.device)
+    else:
+        _check_tensor(out, "out", torch.float32, tex.channels)
+    st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
+    check(tex._lib.htex_lookup_aniso(tex._h, ctypes.c_void_p(queries.data_ptr()), n, int(max_aniso),
+                                     ctypes.c_void_p(out.data_ptr()), _stream(stream), st), "htex_lookup_aniso")
     return out
 
 

@@ -1,0 +1,198 @@
+// Anisotropic filtered lookup and the htex_lookup_aniso entry point.
+//
+// Section 5.1 renders Htex through the GPU's anisotropic filter, applied to
+// each of Alg. 3's three texture fetches; the paper states no formula, so
+// this follows one reading, the same as the FP64 oracle's:
+//   - the footprint is given by the screen derivatives of the barycentrics,
+//     ax = (du/dx, dv/dx) and ay = (du/dy, dv/dy), in quad-uv units;
+//   - px2 = |ax|^2, py2 = |ay|^2 (each product and sum rounded to float);
+//     the major axis m is ay when py2 > px2, else ax; the probe count K is 1
+//     when both are zero, else min(ceil(sqrt(max / min)), kmax), computed
+//     with correctly rounded float division and square root so that the
+//     integer K is decided exactly as the oracle decides it;
+//   - each probe is an isotropic trilinear sample with footprint Pmax / K;
+//   - probe k sits at c + m * s * ((k + 1/2) / K - 1/2) with s = min(1,
+//     K / Pmax) (the probes never span more than K quad widths);
+//   - every probe samples all three fetches at its own (u', v'): own quad
+//     at (u', v'), Next's at (v', -u'), Prev's at (-v', u'), each through
+//     Alg. 2, with full 2x2 zero-bordered taps (a probe off the triangle can
+//     reach any texel of the neighbouring quads); the result is the summed
+//     data over the summed normalisation weight.
+// One thread per query, grid-stride.  A fetch whose quad no probe of any
+// lane of the warp can reach (more than half a coarsest-level texel
+// outside it) is skipped warp-uniformly.
+#include <cuda_runtime.h>
+
+#include "lookup_core.cuh"
+
+namespace htex {
+
+struct AnisoParams {
+    const htex_query_aniso* q;
+    int64_t n;
+    int32_t kmax;
+    float* out;
+    int32_t* status;
+};
+
+// Two taps along one axis for an arbitrary coordinate: index i = floor(s)
+// unclamped, in-bounds weights (zero for a tap outside [0, N)).
+struct TapsG {
+    int i;
+    float w0, w1;
+};
+
+__device__ __forceinline__ TapsG taps_g(float p, int N) {
+    const float s = fmaf(p, float(N), -0.5f);
+    const float fi = floorf(s);
+    const float a = s - fi;
+    const int i = int(fi);
+    return TapsG{i, (i >= 0 && i < N) ? 1.0f - a : 0.0f, (i + 1 >= 0 && i + 1 < N) ? a : 0.0f};
+}
+
+// One level of one fetch at quad coordinates (x, y) with level weight wl.
+template <int DT, int C>
+__device__ __forceinline__ void aniso_level(const Asset<GlobalSpace>& A, const TexRef& t, int l, float x, float y,
+                                            float wl, float sc, float (&acc)[C], float& W) {
+    constexpr int TB = C * Fmt<DT>::ES;
+    const int N = 1 << (t.n - l);
+    const TapsG tx = taps_g(x, N), ty = taps_g(y, N);
+    W += wl * (tx.w0 + tx.w1) * (ty.w0 + ty.w1);
+    const float y0 = ty.w0 * wl, y1 = ty.w1 * wl;
+    const float w[4] = {y0 * tx.w0, y0 * tx.w1, y1 * tx.w0, y1 * tx.w1};
+    const int64_t o = int64_t(t.off) + int64_t(level_texels(t.n, l)) * TB + (int64_t(ty.i) * N + tx.i) * TB;
+    const int64_t d[4] = {0, TB, int64_t(N) * TB, int64_t(N) * TB + TB};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float v[C];
+        load_texel_if<DT, C>(A.pool, w[k] != 0.0f, uint64_t(o + d[k]), v);
+        const float wd = w[k] * sc;
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = fmaf(wd, v[c], acc[c]);
+    }
+}
+
+// One fetch of one probe (one or two levels), skipped when no lane of the
+// warp has a tap in bounds.
+template <int DT, int C>
+__device__ __forceinline__ void aniso_fetch(const Asset<GlobalSpace>& A, unsigned act, bool ok, const TexRef& t,
+                                            const Lod& d, uint32_t code, float a, float b, float (&acc)[C],
+                                            float& W) {
+    const bool flip = code & kFlipBit;
+    const float x = flip ? 1.0f - a : a, y = flip ? 1.0f - b : b;
+    const float half = 0.5f / float(1 << (t.n - coarsest(d)));   // half a texel of the coarsest level read
+    const bool near = ok && x > -half && x < 1.0f + half && y > -half && y < 1.0f + half;
+    if (!__any_sync(act, near)) return;
+    const float sc = code_factor<DT>(t);
+    aniso_level<DT, C>(A, t, d.l0, x, y, near ? d.w0 : 0.0f, sc, acc, W);
+    if (__any_sync(act, near && d.l1 >= 0))
+        aniso_level<DT, C>(A, t, d.l1 >= 0 ? d.l1 : d.l0, x, y, (near && d.l1 >= 0) ? d.w1 : 0.0f, sc, acc, W);
+}
+
+// Probe count (see the file comment): same float operations as the oracle.
+__device__ __forceinline__ int aniso_probes(float px2, float py2, int kmax) {
+    const float mx = fmaxf(px2, py2), mn = fminf(px2, py2);
+    if (mx == 0.0f) return 1;
+    const float r = __fsqrt_rn(__fdiv_rn(mx, mn));
+    if (!(r < float(kmax))) return kmax;
+    return max(1, int(ceilf(r)));
+}
+
+template <int DT, int C>
+__global__ void __launch_bounds__(256) k_lookup_aniso(Asset<GlobalSpace> A, AnisoParams p) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        const int4 r0 = ld_query(reinterpret_cast<const htex_query*>(p.q), 2 * i);
+        const int4 r1 = ld_query(reinterpret_cast<const htex_query*>(p.q), 2 * i + 1);
+        const float dudx = __int_as_float(r1.x), dvdx = __int_as_float(r1.y);
+        const float dudy = __int_as_float(r1.z), dvdy = __int_as_float(r1.w);
+        const float px2 = __fadd_rn(__fmul_rn(dudx, dudx), __fmul_rn(dvdx, dvdx));
+        const float py2 = __fadd_rn(__fmul_rn(dudy, dudy), __fmul_rn(dvdy, dvdy));
+        int h;
+        float u, v, f;
+        bool ok = decode_query(make_int4(r0.x, r0.y, r0.z, 0), A.H, h, u, v, f);
+        ok = ok && isfinite(dudx) && isfinite(dvdx) && isfinite(dudy) && isfinite(dvdy) && isfinite(px2) &&
+             isfinite(py2);
+        if (!ok) {
+            u = 0.0f;
+            v = 0.0f;
+            if (p.status) atomicAdd(p.status, 1);
+        }
+        const int K = ok ? aniso_probes(px2, py2, p.kmax) : 1;
+        const bool major_y = py2 > px2;
+        const float pmax = sqrtf(fmaxf(px2, py2));
+        const float s = pmax > float(K) ? float(K) / pmax : 1.0f;
+        const float mu = (major_y ? dudy : dudx) * s, mv = (major_y ? dvdy : dvdx) * s;
+        const float lf = footprint_log2(ok ? pmax / float(K) : 0.0f);
+
+        const uint4 rec = ok ? A.rec.ld16(uint64_t(h) * 16u) : make_uint4(0, 0, 0, 0);
+        const TexRef to = tex_ref<DT>(A, rec.x & ~kFlipBit);
+        const TexRef tn = tex_ref<DT>(A, rec.y & ~kFlipBit);
+        const TexRef tp = tex_ref<DT>(A, rec.z & ~kFlipBit);
+        const Lod dn0 = select_lod(lf, to.n), dn1 = select_lod(lf, tn.n), dn2 = select_lod(lf, tp.n);
+
+        float acc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+        float W = 0.0f;
+        const unsigned act = __activemask();
+        const int Kw = int(__reduce_max_sync(act, unsigned(K)));   // the warp walks its lanes' largest K
+        for (int k = 0; k < Kw; ++k) {
+            const bool on = ok && k < K;
+            const float t = (float(2 * k + 1) - float(K)) / float(2 * K);
+            const float pu = fmaf(mu, t, u), pv = fmaf(mv, t, v);
+            aniso_fetch<DT, C>(A, act, on, to, dn0, rec.x, pu, pv, acc, W);
+            aniso_fetch<DT, C>(A, act, on, tn, dn1, rec.y, pv, -pu, acc, W);
+            aniso_fetch<DT, C>(A, act, on, tp, dn2, rec.z, -pv, pu, acc, W);
+        }
+        // invalid queries (W = 0, acc = 0): 0 * inf = NaN, as in the isotropic lookup
+        const float inv = __frcp_rn(W);
+        float r[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) r[c] = acc[c] * inv;
+        store_out<C>(p.out, i, r);
+    }
+}
+
+template <int DT, int C>
+htex_status launch_aniso_c(const htex_textures* t, const AnisoParams& p, cudaStream_t s) {
+    const int64_t want = (p.n + 255) / 256;
+    const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * 8);
+    k_lookup_aniso<DT, C><<<unsigned(grid), 256, 0, s>>>(global_asset(t), p);
+    return cudaGetLastError() == cudaSuccess ? HTEX_OK : HTEX_ERR_CUDA;
+}
+
+template <int DT>
+htex_status launch_aniso_dt(const htex_textures* t, const AnisoParams& p, cudaStream_t s) {
+    switch (t->C) {
+    case 1: return launch_aniso_c<DT, 1>(t, p, s);
+    case 2: return launch_aniso_c<DT, 2>(t, p, s);
+    case 3: return launch_aniso_c<DT, 3>(t, p, s);
+    case 4: return launch_aniso_c<DT, 4>(t, p, s);
+    }
+    return HTEX_ERR_INVALID_ARG;
+}
+
+}  // namespace htex
+
+using namespace htex;
+
+extern "C" htex_status htex_lookup_aniso(const htex_textures* t, const htex_query_aniso* q, int64_t n,
+                                         int32_t max_aniso, float* out, htex_stream stream, int32_t* d_status) {
+    if (!t || n < 0 || max_aniso < 1 || max_aniso > 16) return HTEX_ERR_INVALID_ARG;
+    if (n == 0) return HTEX_OK;
+    if (!q || !out) return HTEX_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(q) & 15u) != 0) return HTEX_ERR_INVALID_ARG;
+    const uintptr_t out_align = t->C == 4 ? 16u : (t->C == 2 ? 8u : 4u);
+    if ((reinterpret_cast<uintptr_t>(out) & (out_align - 1)) != 0) return HTEX_ERR_INVALID_ARG;
+    const AnisoParams p{q, n, max_aniso, out, d_status};
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    switch (t->dtype) {
+    case HTEX_F32: return launch_aniso_dt<HTEX_F32>(t, p, s);
+    case HTEX_U8: return launch_aniso_dt<HTEX_U8>(t, p, s);
+    case HTEX_F16: return launch_aniso_dt<HTEX_F16>(t, p, s);
+    case HTEX_BF16: return launch_aniso_dt<HTEX_BF16>(t, p, s);
+    case HTEX_E4M3: return launch_aniso_dt<HTEX_E4M3>(t, p, s);
+    }
+    return HTEX_ERR_INVALID_ARG;
+}

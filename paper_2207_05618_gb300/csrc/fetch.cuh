@@ -278,6 +278,19 @@ struct Asset {
     uint32_t uniform_stride16;  // texture stride / 16 bytes when uniform
 };
 
+// The resident asset of a textures handle, seen from global memory.
+inline Asset<GlobalSpace> global_asset(const htex_textures* t) {
+    Asset<GlobalSpace> A;
+    A.rec.base = static_cast<const uint8_t*>(t->d_rec);
+    A.hdr.base = static_cast<const uint8_t*>(t->d_hdr);
+    A.scale.base = static_cast<const uint8_t*>(t->d_scale);
+    A.pool.base = static_cast<const uint8_t*>(t->d_pool);
+    A.H = t->H;
+    A.uniform_log2n = t->uniform_log2n;
+    A.uniform_stride16 = uint32_t(t->uniform_stride / 16);
+    return A;
+}
+
 struct TexRef {
     uint64_t off;   // byte offset of the texture in the pool
     int n;          // log2 of the resolution

@@ -403,18 +403,6 @@ constexpr uint32_t kMaxStageBytes = 96u * 1024u;
 constexpr int64_t kMinStagedQueries = int64_t(1) << 20;
 constexpr int64_t kBucketTexelBytes = int64_t(32) << 20;
 
-Asset<GlobalSpace> global_asset(const htex_textures* t) {
-    Asset<GlobalSpace> A;
-    A.rec.base = static_cast<const uint8_t*>(t->d_rec);
-    A.hdr.base = static_cast<const uint8_t*>(t->d_hdr);
-    A.scale.base = static_cast<const uint8_t*>(t->d_scale);
-    A.pool.base = static_cast<const uint8_t*>(t->d_pool);
-    A.H = t->H;
-    A.uniform_log2n = t->uniform_log2n;
-    A.uniform_stride16 = uint32_t(t->uniform_stride / 16);
-    return A;
-}
-
 template <class K>
 int resident_blocks(K kernel, int threads, size_t smem) {
     int b = 0;
@@ -609,7 +597,6 @@ extern "C" htex_status htex_queries_sort(const htex_textures* t, const htex_quer
     if (((reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(sorted)) & 15u) != 0 ||
         (reinterpret_cast<uintptr_t>(pos) & 3u) != 0)
         return HTEX_ERR_INVALID_ARG;
-    if (cudaSetDevice(t->device) != cudaSuccess) return HTEX_ERR_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const SortPlan P = sort_plan(t->H);
     cudaMemPool_t pool = scratch_pool(t->device);

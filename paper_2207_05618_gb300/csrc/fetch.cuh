@@ -297,10 +297,13 @@ struct TexRef {
     float scale;    // code scale (1 for unscaled formats)
 };
 
-template <int DT, class S>
+// UNI: the caller knows every texture of the asset has one resolution
+// (uniform_log2n >= 0), so the resolution is the same kernel-wide value for
+// every lane and everything derived from it stays warp-uniform.
+template <int DT, bool UNI = false, class S>
 __device__ __forceinline__ TexRef tex_ref(const Asset<S>& A, uint32_t e) {
     TexRef t;
-    if (A.uniform_log2n >= 0) {
+    if (UNI || A.uniform_log2n >= 0) {
         t.off = uint64_t(e) * A.uniform_stride16 * 16u;
         t.n = A.uniform_log2n;
         t.scale = Fmt<DT>::SCALED ? __uint_as_float(A.scale.ld4(typename S::off_t(e) * 4u)) : 1.0f;
@@ -498,12 +501,14 @@ __device__ __forceinline__ float footprint_log2(float f) {
 }
 
 // Bring a future query's line into L2 (no register, no wait).
-__device__ __forceinline__ void prefetch_query(const htex_query* q, int64_t i) {
+template <class I>
+__device__ __forceinline__ void prefetch_query(const htex_query* q, I i) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const int4*>(q) + i));
 }
 
 // Streaming 16-byte query load: bypasses L1 and is marked first to leave L2.
-__device__ __forceinline__ int4 ld_query(const htex_query* q, int64_t i) {
+template <class I>
+__device__ __forceinline__ int4 ld_query(const htex_query* q, I i) {
     int4 r;
     asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
                  : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)

@@ -28,17 +28,15 @@
 
 namespace htex {
 
-template <bool BINNED>
-__device__ __forceinline__ int64_t dst_of(const FwdParams& p, int64_t i) {
+template <bool BINNED, class I>
+__device__ __forceinline__ int64_t dst_of(const FwdParams& p, I i) {
     return BINNED ? int64_t(__ldcs(p.idx + i)) : i;
 }
 
-// Grid-stride loop, software-pipelined.  Global path (PREF_REC): the query
-// two iterations ahead and the record one iteration ahead are in flight
-// while the current query's texels are gathered.  Staged path: the next
-// query in registers and the one three iterations ahead prefetched into
-// L2 (records are in shared memory).
-template <int DT, int C, bool BINNED, bool PREF_REC, bool DEFER, class S>
+// Grid-stride loop for the global path, software-pipelined: the query two
+// iterations ahead and the record one iteration ahead are in flight while
+// the current query's texels are gathered.
+template <int DT, int C, bool BINNED, bool DEFER, class S>
 __device__ __forceinline__ void lookup_loop(const Asset<S>& A, const FwdParams& p) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -52,41 +50,45 @@ __device__ __forceinline__ void lookup_loop(const Asset<S>& A, const FwdParams& 
         raw1 = ld_query(p.q, i1);
         dst1 = dst_of<BINNED>(p, i1);
     }
-    if constexpr (PREF_REC) {
-        uint4 rec0 = record_of(A, raw0);
-        while (true) {
-            const int64_t i2 = i1 + stride;
-            int4 raw2 = make_int4(-1, 0, 0, 0);
-            int64_t dst2 = 0;
-            if (i2 < p.n) {
-                raw2 = ld_query(p.q, i2);
-                dst2 = dst_of<BINNED>(p, i2);
-            }
-            uint4 rec1 = make_uint4(0, 0, 0, 0);
-            if (i1 < p.n) rec1 = record_of(A, raw1);
-            lookup_one<DT, C, DEFER>(A, p, raw0, rec0, dst0);
-            if (i1 >= p.n) break;
-            raw0 = raw1;
-            dst0 = dst1;
-            rec0 = rec1;
-            raw1 = raw2;
-            dst1 = dst2;
-            i1 = i2;
+    uint4 rec0 = record_of(A, raw0);
+    while (true) {
+        const int64_t i2 = i1 + stride;
+        int4 raw2 = make_int4(-1, 0, 0, 0);
+        int64_t dst2 = 0;
+        if (i2 < p.n) {
+            raw2 = ld_query(p.q, i2);
+            dst2 = dst_of<BINNED>(p, i2);
         }
-    } else {
-        while (true) {
-            if (i1 + 2 * stride < p.n) prefetch_query(p.q, i1 + 2 * stride);
-            lookup_one<DT, C, DEFER>(A, p, raw0, record_of(A, raw0), dst0);
-            if (i1 >= p.n) break;
-            raw0 = raw1;
-            dst0 = dst1;
-            const int64_t i2 = i1 + stride;
-            if (i2 < p.n) {
-                raw1 = ld_query(p.q, i2);
-                dst1 = dst_of<BINNED>(p, i2);
-            }
-            i1 = i2;
-        }
+        uint4 rec1 = make_uint4(0, 0, 0, 0);
+        if (i1 < p.n) rec1 = record_of(A, raw1);
+        lookup_one<DT, C, DEFER>(A, p, raw0, rec0, dst0);
+        if (i1 >= p.n) break;
+        raw0 = raw1;
+        dst0 = dst1;
+        rec0 = rec1;
+        raw1 = raw2;
+        dst1 = dst2;
+        i1 = i2;
+    }
+}
+
+// Grid-stride loop for the shared-memory path, two queries per thread and
+// iteration: both queries and both records are loaded before either is
+// filtered, so their latencies overlap; the pair four strides ahead is
+// prefetched into L2.  I: the index type (32-bit when n allows).
+template <int DT, int C, bool BINNED, bool DEFER, bool UNI, class I, class S>
+__device__ __forceinline__ void lookup_loop_pairs(const Asset<S>& A, const FwdParams& p) {
+    const I n = I(p.n);
+    const I stride = I(gridDim.x) * I(blockDim.x);
+    for (I i = I(blockIdx.x) * I(blockDim.x) + I(threadIdx.x); i < n; i += 2 * stride) {
+        const I j = i + stride;
+        const int4 ra = ld_query(p.q, i);
+        const int4 rb = j < n ? ld_query(p.q, j) : make_int4(-1, 0, 0, 0);
+        if (i + 4 * stride < n) prefetch_query(p.q, i + 4 * stride);
+        if (j + 4 * stride < n) prefetch_query(p.q, j + 4 * stride);
+        const uint4 ca = record_of(A, ra), cb = record_of(A, rb);
+        lookup_one<DT, C, DEFER, UNI>(A, p, ra, ca, dst_of<BINNED>(p, i));
+        if (j < n) lookup_one<DT, C, DEFER, UNI>(A, p, rb, cb, dst_of<BINNED>(p, j));
     }
 }
 
@@ -98,7 +100,7 @@ constexpr int kStagedThreads = 384;
 
 template <int DT, int C, bool BINNED>
 __global__ void __launch_bounds__(kGlobalThreads, HTEX_GLOBAL_MIN_BLOCKS) k_lookup_global(Asset<GlobalSpace> A, FwdParams p) {
-    lookup_loop<DT, C, BINNED, true, Raw<DT, C>::PACKED>(A, p);
+    lookup_loop<DT, C, BINNED, Raw<DT, C>::PACKED>(A, p);
 }
 
 // Shared-memory layout of a staged asset: records, headers, scales, pool,
@@ -123,7 +125,7 @@ __device__ __forceinline__ void stage16(uint8_t* dst, const void* src, uint32_t 
     for (uint32_t k = threadIdx.x; k < bytes / 16u; k += blockDim.x) d[k] = __ldg(s + k);
 }
 
-template <int DT, int C, bool BINNED>
+template <int DT, int C, bool BINNED, bool UNI>
 __global__ void __launch_bounds__(kStagedThreads, 3) k_lookup_staged(Asset<GlobalSpace> G, int32_t E,
                                                                   int64_t pool_bytes, FwdParams p) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -141,7 +143,10 @@ __global__ void __launch_bounds__(kStagedThreads, 3) k_lookup_staged(Asset<Globa
     A.H = G.H;
     A.uniform_log2n = G.uniform_log2n;
     A.uniform_stride16 = G.uniform_stride16;
-    lookup_loop<DT, C, BINNED, false, false>(A, p);
+    if (p.n <= int64_t(INT32_MAX) - 4 * int64_t(gridDim.x) * blockDim.x)
+        lookup_loop_pairs<DT, C, BINNED, false, UNI, int32_t>(A, p);
+    else
+        lookup_loop_pairs<DT, C, BINNED, false, UNI, int64_t>(A, p);
 }
 
 // ------------------------------------------------------------------ binning
@@ -417,7 +422,7 @@ htex_status launch_fwd(const htex_textures* t, const FwdParams& p, uint32_t flag
     const bool staged = !(flags & HTEX_LOOKUP_GLOBAL) && int64_t(L.total) <= int64_t(kMaxStageBytes) &&
                         p.n >= kMinStagedQueries;
     if (staged) {
-        auto k = k_lookup_staged<DT, C, BINNED>;
+        auto k = t->uniform_log2n >= 0 ? k_lookup_staged<DT, C, BINNED, true> : k_lookup_staged<DT, C, BINNED, false>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L.total)) != cudaSuccess)
             return HTEX_ERR_CUDA;
         const int64_t want = (p.n + kStagedThreads - 1) / kStagedThreads;

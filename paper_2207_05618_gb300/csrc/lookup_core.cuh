@@ -151,15 +151,15 @@ __device__ __forceinline__ void edge_fetch(const Asset<S>& A, unsigned act, bool
 // Every load of nonzero weight is issued without branching; parts no lane
 // of the warp needs are skipped warp-uniformly.  L0: no lane of the warp
 // has a positive footprint, so every fetch is level 0 only.
-template <int DT, int C, bool L0, bool DEFER, class S>
+template <int DT, int C, bool L0, bool DEFER, bool UNI, class S>
 __device__ __forceinline__ void lookup_body(const Asset<S>& A, const FwdParams& p, unsigned act, bool ok, float u,
                                             float v, float f, uint4 rec, int64_t dst) {
-    const bool uni = A.uniform_log2n >= 0;
+    const bool uni = UNI || A.uniform_log2n >= 0;
     const float lf = L0 ? -__int_as_float(0x7f800000) : footprint_log2(f);
     Gather<DT, C, DEFER> g;
 
     // own quad at (u, v), through Alg. 2
-    const TexRef to = tex_ref<DT>(A, rec.x & ~kFlipBit);
+    const TexRef to = tex_ref<DT, UNI>(A, rec.x & ~kFlipBit);
     const Lod d = L0 ? Lod{0, -1, 1.0f, 0.0f} : select_lod(lf, to.n);
     const bool fo = rec.x & kFlipBit;
     const float x = fo ? 1.0f - u : u, y = fo ? 1.0f - v : v;
@@ -170,8 +170,8 @@ __device__ __forceinline__ void lookup_body(const Asset<S>& A, const FwdParams& 
     }
 
     // which edge fetches have taps in bounds (at the coarsest level read)
-    const TexRef tn = tex_ref<DT>(A, rec.y & ~kFlipBit);
-    const TexRef tp = tex_ref<DT>(A, rec.z & ~kFlipBit);
+    const TexRef tn = tex_ref<DT, UNI>(A, rec.y & ~kFlipBit);
+    const TexRef tp = tex_ref<DT, UNI>(A, rec.z & ~kFlipBit);
     const Lod dn = (L0 || uni) ? d : select_lod(lf, tn.n);
     const Lod dp = (L0 || uni) ? d : select_lod(lf, tp.n);
     const bool nn = ok && across_weight(u, 1 << (tn.n - coarsest(dn))) > 0.0f;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void lookup_body(const Asset<S>& A, const FwdParams& 
     store_out<C>(p.out, dst, r);
 }
 
-template <int DT, int C, bool DEFER, class S>
+template <int DT, int C, bool DEFER, bool UNI = false, class S>
 __device__ __forceinline__ void lookup_one(const Asset<S>& A, const FwdParams& p, int4 raw, uint4 rec,
                                            int64_t dst) {
     int h;
@@ -207,8 +207,8 @@ __device__ __forceinline__ void lookup_one(const Asset<S>& A, const FwdParams& p
         if (p.status) atomicAdd(p.status, 1);
     }
     const unsigned act = __activemask();
-    if (__any_sync(act, f > 0.0f)) lookup_body<DT, C, false, DEFER>(A, p, act, ok, u, v, f, rec, dst);
-    else lookup_body<DT, C, true, DEFER>(A, p, act, ok, u, v, f, rec, dst);
+    if (__any_sync(act, f > 0.0f)) lookup_body<DT, C, false, DEFER, UNI>(A, p, act, ok, u, v, f, rec, dst);
+    else lookup_body<DT, C, true, DEFER, UNI>(A, p, act, ok, u, v, f, rec, dst);
 }
 
 }  // namespace htex

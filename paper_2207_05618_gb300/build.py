@@ -36,7 +36,11 @@ def _compile(src: str) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     inc = ["-I", INCLUDE, "-I", CSRC]
     if src.endswith(".cu"):
-        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        # -fmad=false: no implicit multiply-add contraction, so every kernel
+        # instantiation (plain, sorted, staged, serving) rounds exactly the
+        # arithmetic as written and their results agree bit for bit;
+        # explicit fmaf() calls stay fused.
+        cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
                "-Xcompiler", "-ffp-contract=off", "-Xptxas", "-O3", *inc, "-c", src, "-o", obj]
     else:
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", *inc,

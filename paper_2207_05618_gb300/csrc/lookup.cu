@@ -35,34 +35,36 @@ __device__ __forceinline__ int64_t dst_of(const FwdParams& p, I i) {
 
 // Grid-stride loop for the global path, software-pipelined: the query two
 // iterations ahead and the record one iteration ahead are in flight while
-// the current query's texels are gathered.
-template <int DT, int C, bool BINNED, bool DEFER, class S>
+// the current query's texels are gathered.  I: the index type (32-bit when
+// n allows); UNI: every texture has one resolution.
+template <int DT, int C, bool BINNED, bool DEFER, bool UNI, class I, class S>
 __device__ __forceinline__ void lookup_loop(const Asset<S>& A, const FwdParams& p) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i0 >= p.n) return;
-    int64_t i1 = i0 + stride;
+    const I n = I(p.n);
+    const I stride = I(gridDim.x) * I(blockDim.x);
+    I i0 = I(blockIdx.x) * I(blockDim.x) + I(threadIdx.x);
+    if (i0 >= n) return;
+    I i1 = i0 + stride;
     int4 raw0 = ld_query(p.q, i0);
     int64_t dst0 = dst_of<BINNED>(p, i0);
     int4 raw1 = make_int4(-1, 0, 0, 0);
     int64_t dst1 = 0;
-    if (i1 < p.n) {
+    if (i1 < n) {
         raw1 = ld_query(p.q, i1);
         dst1 = dst_of<BINNED>(p, i1);
     }
     uint4 rec0 = record_of(A, raw0);
     while (true) {
-        const int64_t i2 = i1 + stride;
+        const I i2 = i1 + stride;
         int4 raw2 = make_int4(-1, 0, 0, 0);
         int64_t dst2 = 0;
-        if (i2 < p.n) {
+        if (i2 < n) {
             raw2 = ld_query(p.q, i2);
             dst2 = dst_of<BINNED>(p, i2);
         }
         uint4 rec1 = make_uint4(0, 0, 0, 0);
-        if (i1 < p.n) rec1 = record_of(A, raw1);
-        lookup_one<DT, C, DEFER>(A, p, raw0, rec0, dst0);
-        if (i1 >= p.n) break;
+        if (i1 < n) rec1 = record_of(A, raw1);
+        lookup_one<DT, C, DEFER, UNI>(A, p, raw0, rec0, dst0);
+        if (i1 >= n) break;
         raw0 = raw1;
         dst0 = dst1;
         rec0 = rec1;
@@ -98,9 +100,12 @@ constexpr int kGlobalThreads = 256;
 #endif
 constexpr int kStagedThreads = 384;
 
-template <int DT, int C, bool BINNED>
+template <int DT, int C, bool BINNED, bool UNI>
 __global__ void __launch_bounds__(kGlobalThreads, HTEX_GLOBAL_MIN_BLOCKS) k_lookup_global(Asset<GlobalSpace> A, FwdParams p) {
-    lookup_loop<DT, C, BINNED, Raw<DT, C>::PACKED>(A, p);
+    if (p.n <= int64_t(INT32_MAX) - 2 * int64_t(gridDim.x) * blockDim.x)
+        lookup_loop<DT, C, BINNED, Raw<DT, C>::PACKED, UNI, int32_t>(A, p);
+    else
+        lookup_loop<DT, C, BINNED, Raw<DT, C>::PACKED, UNI, int64_t>(A, p);
 }
 
 // Shared-memory layout of a staged asset: records, headers, scales, pool,
@@ -429,7 +434,7 @@ htex_status launch_fwd(const htex_textures* t, const FwdParams& p, uint32_t flag
         const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * resident_blocks(k, kStagedThreads, L.total));
         k<<<unsigned(grid), kStagedThreads, L.total, s>>>(A, t->E, t->pool_bytes, p);
     } else {
-        auto k = k_lookup_global<DT, C, BINNED>;
+        auto k = t->uniform_log2n >= 0 ? k_lookup_global<DT, C, BINNED, true> : k_lookup_global<DT, C, BINNED, false>;
         const int64_t want = (p.n + kGlobalThreads - 1) / kGlobalThreads;
         const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * resident_blocks(k, kGlobalThreads, 0));
         k<<<unsigned(grid), kGlobalThreads, 0, s>>>(A, p);

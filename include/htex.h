@@ -321,12 +321,16 @@ htex_status htex_results_gather(const float* sorted_out, const int32_t* pos, int
 /* htex_lookup on host buffers (the end-to-end path for callers whose
  * queries and results live in host memory).
  *   q    host [n] htex_query;  out  host [n][channels] float
- * The queries go to the device and the results come back in chunks of
- * 2,097,152, each chunk on one of three library-owned streams, so that the
- * copy in of one chunk, the lookup of another and the copy out of a third
- * overlap.  Copies overlap only from page-locked host memory (e.g.
- * cudaHostAlloc, torch pin_memory); pageable buffers still give correct
- * results.  The first call on a textures object creates its streams and
+ * When both buffers are page-locked and mapped into the device's address
+ * space (cudaHostAlloc, torch pin_memory, cudaHostRegister with mapping)
+ * and aligned as htex_lookup requires, the lookup kernels read the queries
+ * and write the results across the link in place, in one pass
+ * (HTEX_LOOKUP_BIN is then ignored: its sort would read the queries across
+ * the link twice more).  Otherwise the queries go to the device and the
+ * results come back in chunks of 2,097,152, each chunk on one of three
+ * library-owned streams, so that the copy in of one chunk, the lookup of
+ * another and the copy out of a third overlap; pageable buffers give the
+ * same results, without overlap.  The first call on a textures object creates its streams and
  * about 200 MB of device staging (freed by htex_textures_destroy; returns
  * HTEX_ERR_OUT_OF_MEMORY if that fails).  Ordered after earlier work on
  * 'stream' and asynchronous: 'out' is complete once 'stream' is; 'q' and

@@ -1,5 +1,10 @@
-// htex_lookup_host: filtered lookups on host buffers.  The queries are
-// copied in and the results out in chunks, each chunk on one of three
+// htex_lookup_host: filtered lookups on host buffers.  When both buffers
+// are page-locked and mapped into the device's address space (and aligned
+// as the kernels need), the lookup kernels read the queries and write the
+// results across the CPU-GPU link directly: the filter is bound by its
+// texel gathers, so reading the queries from host memory costs almost
+// nothing and no staging copy is needed.  Otherwise the queries are copied
+// in and the results out in chunks, each chunk on one of three
 // library-owned streams in turn, so that the host-to-device copy of one
 // chunk, the lookup kernel of another and the device-to-host copy of a
 // third run at the same time.  The caller's stream orders the whole call:
@@ -15,6 +20,17 @@ namespace {
 
 constexpr int kStages = 3;
 constexpr int64_t kChunk = int64_t(1) << 21;   // queries per chunk
+
+// Device address of a page-locked, mapped host buffer (null for any other
+// memory, which the kernels must not touch).
+const void* mapped_address(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
 
 }  // namespace
 
@@ -72,6 +88,17 @@ extern "C" htex_status htex_lookup_host(const htex_textures* t, const htex_query
     int device = -1;
     if (cudaGetDevice(&device) != cudaSuccess) return HTEX_ERR_CUDA;
     if (device != t->device) return HTEX_ERR_INVALID_ARG;
+    {
+        const void* mq = mapped_address(q);
+        const void* mo = mapped_address(out);
+        const uintptr_t out_align = t->C == 4 ? 16u : (t->C == 2 ? 8u : 4u);
+        if (mq && mo && (reinterpret_cast<uintptr_t>(mq) & 15u) == 0 &&
+            (reinterpret_cast<uintptr_t>(mo) & (out_align - 1)) == 0)
+            // one pass in place: sorting would read the queries across the link twice more
+            return htex_launch_lookup(t, static_cast<const htex_query*>(mq), n,
+                                      static_cast<float*>(const_cast<void*>(mo)), flags & ~uint32_t(HTEX_LOOKUP_BIN),
+                                      stream, d_status);
+    }
     htex_textures* tm = const_cast<htex_textures*>(t);
     static std::mutex create_mu;
     {

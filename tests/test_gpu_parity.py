@@ -338,21 +338,26 @@ def test_backward_matches_oracle_gradient(fmt, C):
 
 # ------------------------------------------------------------------- host path
 
-@pytest.mark.parametrize("pinned", [True, False])
-def test_lookup_host_matches_device_lookup(pinned):
-    """htex_lookup_host (chunks of 2^21 over three internal streams) gives
-    the device lookup's results bit for bit, across chunk boundaries and a
-    ragged tail, from pinned and from pageable host memory."""
+@pytest.mark.parametrize("mode", ["pinned", "pageable", "mixed", "misaligned"])
+def test_lookup_host_matches_device_lookup(mode):
+    """htex_lookup_host gives the device lookup's results bit for bit, in
+    place on pinned memory and through chunks of 2^21 over three internal
+    streams otherwise (pageable buffers, a pinned/pageable mix, a pinned
+    result buffer misaligned for 16-byte stores), across chunk boundaries
+    and a ragged tail."""
     gen = lambda: syn.cylinder(around=32, rows=16, seed=11)
     mo, to, tl, *_ = _case(gen, _u(6), 4, "u8", hx.BUILD_MIPS, seed=12)
     n = 2 * (1 << 21) + 13
     qs = syn.queries(mo.H, n, seed=13, footprint="loguniform")
     qh = torch.from_numpy(hx.pack_queries(*qs))
-    if pinned:
+    if mode != "pageable":
         qh = qh.pin_memory()
-    out = torch.empty((n, 4), dtype=torch.float32)
-    out = out.pin_memory() if pinned else out
-    hx.lookup_host(tl, qh, out=out)
+    if mode == "misaligned":
+        out = torch.empty(n * 4 + 1, dtype=torch.float32).pin_memory()[1:].view(n, 4)
+    else:
+        out = torch.empty((n, 4), dtype=torch.float32)
+        out = out.pin_memory() if mode == "pinned" else out
+    hx.lookup_host(tl, qh, out=out, flags=hx.LOOKUP_BIN if mode == "pinned" else 0)
     torch.cuda.synchronize()
     ref = hx.lookup(tl, qh.cuda()).cpu()
     torch.cuda.synchronize()

@@ -683,6 +683,9 @@ def backward_bench(hx, torch, stream):
     grad = torch.zeros(tex.pool_elements, dtype=torch.float32, device="cuda")
     fwd_ms = timed(torch, stream, lambda: hx.lookup(target, q, stream=stream), 50)
     bwd_ms = timed(torch, stream, lambda: hx.lookup_backward(target, q, g, grad_texels=grad, stream=stream), 50)
+    fwd_sorted_ms = timed(torch, stream, lambda: hx.lookup(target, q, flags=hx.LOOKUP_BIN, stream=stream), 50)
+    bwd_sorted_ms = timed(torch, stream, lambda: hx.lookup_backward(target, q, g, grad_texels=grad,
+                                                                    flags=hx.LOOKUP_BIN, stream=stream), 50)
 
     def batches(step):
         qq = device_queries(torch, mesh.H, n, gen)
@@ -693,6 +696,8 @@ def backward_bench(hx, torch, stream):
     tex.close()
     return {"halfedges": mesh.H, "edges": mesh.E, "queries": n,
             "forward_lookups_per_s": n / (fwd_ms / 1e3), "backward_queries_per_s": n / (bwd_ms / 1e3),
+            "forward_sorted_lookups_per_s": n / (fwd_sorted_ms / 1e3),
+            "backward_sorted_queries_per_s": n / (bwd_sorted_ms / 1e3),
             "fit": {"steps": r.steps, "initial_loss": r.losses[0], "final_loss": r.losses[-1],
                     "final_over_initial": r.ratio, "ms_per_step": r.seconds * 1e3 / r.steps,
                     "loss_every_20": r.losses[::20]}}

@@ -347,6 +347,12 @@ htex_status htex_lookup_host(const htex_textures* t, const htex_query* q, int64_
  *   grad_texels  device float, one per pool element (pool_bytes / element
  *                size), same element order as the pool; accumulated into
  *                (the caller zeroes it); padding elements stay untouched
+ *   flags        HTEX_LOOKUP_BIN: when the pool exceeds 64 MiB, sort the
+ *                queries as htex_lookup does (chunks of 2^23, ranges of
+ *                consecutive halfedges; grad_out rows follow their queries)
+ *                so that neighbouring threads add into neighbouring
+ *                textures; scratch of 20 + 4 * channels bytes per chunk
+ *                query from the library pool.  HTEX_LOOKUP_GLOBAL ignored.
  *   d_status     as for htex_lookup
  * Uses float atomics: the summation order, hence the last bits, may vary
  * from run to run.  Asynchronous. */

@@ -198,6 +198,6 @@ extern "C" htex_status htex_lookup_backward(const htex_textures* t, const htex_q
     // vector atomics need the gradient's texel groups aligned to their size
     const uintptr_t ga = t->C == 4 ? 16u : (t->C == 2 ? 8u : 4u);
     if ((reinterpret_cast<uintptr_t>(grad_texels) & (ga - 1)) != 0) return HTEX_ERR_INVALID_ARG;
-    if (flags & HTEX_LOOKUP_BIN) return HTEX_ERR_UNSUPPORTED;
+    if (flags & HTEX_LOOKUP_BIN) return htex_launch_backward_sorted(t, q, n, grad_out, grad_texels, stream, d_status);
     return htex_launch_backward(t, q, n, grad_out, grad_texels, flags, stream, d_status);
 }

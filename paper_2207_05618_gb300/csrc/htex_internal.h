@@ -104,3 +104,9 @@ htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int6
 htex_status htex_launch_backward(const htex_textures* t, const htex_query* q, int64_t n,
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);
+// The adjoint on queries sorted by halfedge range (HTEX_LOOKUP_BIN), chunk
+// by chunk: the scatter-adds of neighbouring threads land in neighbouring
+// textures.  Falls back to the unsorted adjoint for pools that fit L2.
+htex_status htex_launch_backward_sorted(const htex_textures* t, const htex_query* q, int64_t n,
+                                        const float* grad_out, float* grad_texels, htex_stream stream,
+                                        int32_t* d_status);

@@ -364,6 +364,24 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const htex_query
     }
 }
 
+// Rows of a per-query array into sorted order: rows[pos[i]] = src[i] (the
+// adjoint's upstream gradients follow their queries).
+template <int C>
+__global__ void k_chunk_permute(const float* src, const int32_t* pos, int64_t m, float* rows) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int64_t p = __ldcs(pos + i);
+        if constexpr (C == 4) {
+            reinterpret_cast<float4*>(rows)[p] = __ldcs(reinterpret_cast<const float4*>(src) + i);
+        } else if constexpr (C == 2) {
+            reinterpret_cast<float2*>(rows)[p] = __ldcs(reinterpret_cast<const float2*>(src) + i);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) rows[p * C + c] = __ldcs(src + i * C + c);
+        }
+    }
+}
+
 // Results back in query order: out[i] = sorted_out[pos[i]] (NaN where
 // pos[i] is not in [0, m)).
 template <int C>
@@ -594,6 +612,51 @@ htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int6
         st = launch_sort(t, P, q + c0, m, counters, sq, pos, 0, s);
         if (st == HTEX_OK) st = launch_fwd_dt<false>(t, FwdParams{sq, m, sout, d_status, nullptr}, fwd_flags, s);
         if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, t->num_sms, s);
+    }
+    cudaFreeAsync(scratch, s);
+    return st;
+}
+
+htex_status htex_launch_backward_sorted(const htex_textures* t, const htex_query* q, int64_t n,
+                                        const float* grad_out, float* grad_texels, htex_stream stream,
+                                        int32_t* d_status) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (htex_bin_shift(t) < 0) return htex_launch_backward(t, q, n, grad_out, grad_texels, 0u, stream, d_status);
+    const SortPlan P = sort_plan(t->H);
+    const int64_t M = std::min<int64_t>(n, kSortChunk);
+    const size_t cnt_b = counter_bytes(P);
+    const size_t sq_b = size_t(M) * 16, pos_b = (size_t(M) * 4 + 255) & ~size_t(255);
+    const size_t g_b = size_t(M) * 4 * size_t(t->C);
+    cudaMemPool_t pool = scratch_pool(t->device);
+    if (!pool) return HTEX_ERR_CUDA;
+    void* scratch = nullptr;
+    if (cudaMallocFromPoolAsync(&scratch, cnt_b + sq_b + pos_b + g_b, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return HTEX_ERR_OUT_OF_MEMORY;
+    }
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    uint32_t* counters = reinterpret_cast<uint32_t*>(base);
+    htex_query* sq = reinterpret_cast<htex_query*>(base + cnt_b);
+    int32_t* pos = reinterpret_cast<int32_t*>(base + cnt_b + sq_b);
+    float* gs = reinterpret_cast<float*>(base + cnt_b + sq_b + pos_b);
+    const unsigned g = unsigned(std::max(1, t->num_sms)) * 8;
+    htex_status st = HTEX_OK;
+    for (int64_t c0 = 0; c0 < n && st == HTEX_OK; c0 += M) {
+        const int64_t m = std::min<int64_t>(M, n - c0);
+        st = launch_sort(t, P, q + c0, m, counters, sq, pos, 0, s);
+        if (st != HTEX_OK) break;
+        const float* gsrc = grad_out + c0 * t->C;
+        switch (t->C) {
+        case 1: k_chunk_permute<1><<<g, 256, 0, s>>>(gsrc, pos, m, gs); break;
+        case 2: k_chunk_permute<2><<<g, 256, 0, s>>>(gsrc, pos, m, gs); break;
+        case 3: k_chunk_permute<3><<<g, 256, 0, s>>>(gsrc, pos, m, gs); break;
+        default: k_chunk_permute<4><<<g, 256, 0, s>>>(gsrc, pos, m, gs); break;
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            st = HTEX_ERR_CUDA;
+            break;
+        }
+        st = htex_launch_backward(t, sq, m, gs, grad_texels, 0u, stream, d_status);
     }
     cudaFreeAsync(scratch, s);
     return st;

@@ -77,3 +77,39 @@ def test_fit_to_smooth_target():
     res = fit.fit(tex, batches, steps=80, lr=0.05)
     assert all(np.isfinite(res.losses))
     assert res.ratio < 0.02, res.losses[::10]
+
+
+def test_sorted_backward_matches_unsorted_and_oracle():
+    """HTEX_LOOKUP_BIN on the adjoint: queries sorted by halfedge range in
+    chunks of 2^23 with their upstream gradients following them (a full
+    chunk plus a ragged one, invalid queries inside), on a pool above the
+    64 MiB threshold.  The gradient equals the unsorted kernel's and the
+    oracle's up to float-atomic reordering (1e-5 relative to the largest
+    entry)."""
+    import oracle
+    fs, fv, V, _ = syn.cylinder(around=128, rows=60, seed=14)
+    mesh = hx.Mesh(fs, fv, V)
+    mo = oracle.mesh_from_faces(fs, fv, V)
+    log2n = np.full(mesh.E, 5, np.int32)
+    tex_np = syn.texels_f32(log2n, 1, seed=15)
+    tex = hx.Textures.upload(mesh, log2n, tex_np, 1, "f32", hx.BUILD_MIPS)
+    assert tex.pool_bytes > (64 << 20)
+    n = (1 << 23) + 4099
+    h, u, v, f = syn.queries(mesh.H, n, seed=16, footprint="loguniform", lo=-7, hi=0.5)
+    h[::50021] = -1
+    q = torch.from_numpy(hx.pack_queries(h, u, v, f)).cuda()
+    g = torch.from_numpy(np.random.default_rng(17).standard_normal((n, 1)).astype(np.float32)).cuda()
+    s0 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a = hx.lookup_backward(tex, q, g, status=s0).double().cpu().numpy()
+    b = hx.lookup_backward(tex, q, g, flags=hx.LOOKUP_BIN, status=s1).double().cpu().numpy()
+    assert int(s0.item()) == int(s1.item()) == int((h < 0).sum())
+    scale = np.abs(a).max()
+    assert np.abs(a - b).max() <= 1e-5 * scale
+    # oracle on the first 200k queries (the gradient is a sum over queries)
+    k = 200000
+    to = oracle.prepare_textures(mo, log2n, tex_np, 1, "f32", hx.BUILD_MIPS)
+    ref = oracle.grad_to_pool_layout(to, oracle.lookup_grad(mo, to, (h[:k], u[:k], v[:k], f[:k]),
+                                                            g[:k].cpu().numpy().astype(np.float64)), 4)
+    c = hx.lookup_backward(tex, q[:k], g[:k], flags=hx.LOOKUP_BIN).double().cpu().numpy()
+    assert np.abs(c - ref[:c.shape[0]]).max() <= 1e-5 * max(np.abs(ref).max(), 1.0)

@@ -360,6 +360,21 @@ htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, in
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);
 
+/* One Adam step on the texels of an FP32 asset, for fitting textures from
+ * the gradients of htex_lookup_backward (no counterpart in the paper).  Per
+ * element, with t = step:
+ *   m = beta1 m + (1 - beta1) g;  v = beta2 v + (1 - beta2) g^2;
+ *   master -= (lr / (1 - beta1^t)) m / (sqrt(v) / sqrt(1 - beta2^t) + eps)
+ * then the new value is written into the resident pool (the next lookup
+ * sees it) and g is set to 0 (ready for the next accumulation).
+ *   master, grad, m, v  device float [n], 16-byte aligned, n = pool_bytes
+ *                       / 4 (pool element order, as htex_lookup_backward)
+ *   step                >= 1; beta1, beta2 in [0, 1); eps > 0
+ * HTEX_ERR_INVALID_ARG for other formats or sizes.  Asynchronous. */
+htex_status htex_textures_adam_step(htex_textures* t, float* master, float* grad, float* m, float* v, int64_t n,
+                                    float lr, float beta1, float beta2, float eps, int32_t step,
+                                    htex_stream stream);
+
 /* -------------------------------------------------------------- rendering */
 
 /* The step before the lookup in the paper's pipeline (Section 4.4,

@@ -181,6 +181,20 @@ class Textures:
         check(self._lib.htex_textures_write_pool(self._h, int(offset), int(nbytes), ptr, _stream(stream)),
               "htex_textures_write_pool")
 
+    def adam_step(self, master, grad, m, v, step: int, lr: float, betas=(0.9, 0.999), eps: float = 1e-8,
+                  stream=None) -> None:
+        """htex_textures_adam_step: one Adam step on an FP32 asset's texels;
+        updates master, m and v, writes the new values into the pool and
+        clears grad (all float32 CUDA tensors of pool_elements)."""
+        import torch
+        for name, x in (("master", master), ("grad", grad), ("m", m), ("v", v)):
+            if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+                    and x.numel() == self.pool_elements):
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of pool_elements")
+        check(self._lib.htex_textures_adam_step(self._h, *[ctypes.c_void_p(x.data_ptr()) for x in (master, grad, m, v)],
+                                                self.pool_elements, float(lr), float(betas[0]), float(betas[1]),
+                                                float(eps), int(step), _stream(stream)), "htex_textures_adam_step")
+
     @property
     def pool_elements(self) -> int:
         return self.pool_bytes // ELEM_SIZE[self.dtype]

@@ -60,6 +60,8 @@ _SIGNATURES = {
     "htex_queries_sort": ([P, P, I64, P, P, P], I32),
     "htex_results_gather": ([P, P, I64, I32, P, P], I32),
     "htex_lookup_backward": ([P, P, I64, P, P, U32, P, P], I32),
+    "htex_textures_adam_step": ([P, P, P, P, P, I64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, I32, P], I32),
     "htex_lookup_host": ([P, P, I64, P, U32, P, P], I32),
     "htex_geometry_create": ([P, P, P, PP], I32),
     "htex_geometry_destroy": ([P], None),

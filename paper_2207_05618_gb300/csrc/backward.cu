@@ -7,6 +7,9 @@
 // loads), then scatter-adds grad_out * w_k / W into every in-bounds tap
 // with nonzero weight: float4/float2 atomics where a texel's channels are
 // contiguous and aligned, scalar atomics otherwise.
+#include <algorithm>
+#include <cmath>
+
 #include <cuda_runtime.h>
 
 #include "fetch.cuh"
@@ -185,6 +188,81 @@ htex_status htex_launch_backward(const htex_textures* t, const htex_query* q, in
     case HTEX_E4M3: return launch_bwd_c<HTEX_E4M3>(t, p, s);
     }
     return HTEX_ERR_INVALID_ARG;
+}
+
+// ------------------------------------------------------ Adam on the pool
+//
+// One Adam step (Kingma & Ba) on an FP32 asset's texels, fused with what a
+// texture fit needs around it: the updated values go to the master copy
+// and straight into the resident pool, and the gradient is cleared for the
+// next accumulation.  Per element, with t the step number:
+//   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+//   p = p - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps).
+struct AdamParams {
+    float* master;
+    float* grad;
+    float* m;
+    float* v;
+    float* pool;
+    int64_t n;
+    float b1, b2, eps, step_size, inv_sqrt_bc2;
+};
+
+__device__ __forceinline__ float adam_one(float& p, float g, float& m, float& v, const AdamParams& a) {
+    m = fmaf(a.b1, m, (1.0f - a.b1) * g);
+    v = fmaf(a.b2, v, ((1.0f - a.b2) * g) * g);
+    const float denom = sqrtf(v) * a.inv_sqrt_bc2 + a.eps;
+    p = p - a.step_size * (m / denom);
+    return p;
+}
+
+__global__ void __launch_bounds__(256) k_adam(AdamParams a) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int64_t n4 = a.n / 4;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        float4 p = reinterpret_cast<float4*>(a.master)[i];
+        const float4 g = __ldcs(reinterpret_cast<const float4*>(a.grad) + i);
+        float4 m = reinterpret_cast<float4*>(a.m)[i];
+        float4 v = reinterpret_cast<float4*>(a.v)[i];
+        adam_one(p.x, g.x, m.x, v.x, a);
+        adam_one(p.y, g.y, m.y, v.y, a);
+        adam_one(p.z, g.z, m.z, v.z, a);
+        adam_one(p.w, g.w, m.w, v.w, a);
+        reinterpret_cast<float4*>(a.master)[i] = p;
+        reinterpret_cast<float4*>(a.m)[i] = m;
+        reinterpret_cast<float4*>(a.v)[i] = v;
+        __stcs(reinterpret_cast<float4*>(a.pool) + i, p);
+        __stcs(reinterpret_cast<float4*>(a.grad) + i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+    }
+    for (int64_t i = 4 * n4 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        float p = a.master[i], m = a.m[i], v = a.v[i];
+        adam_one(p, a.grad[i], m, v, a);
+        a.master[i] = p;
+        a.m[i] = m;
+        a.v[i] = v;
+        a.pool[i] = p;
+        a.grad[i] = 0.0f;
+    }
+}
+
+extern "C" htex_status htex_textures_adam_step(htex_textures* t, float* master, float* grad, float* m, float* v,
+                                               int64_t n, float lr, float beta1, float beta2, float eps,
+                                               int32_t step, htex_stream stream) {
+    if (!t || t->dtype != HTEX_F32) return HTEX_ERR_INVALID_ARG;
+    if (n != t->pool_bytes / 4 || step < 1) return HTEX_ERR_INVALID_ARG;
+    if (!master || !grad || !m || !v) return HTEX_ERR_INVALID_ARG;
+    const uintptr_t all = reinterpret_cast<uintptr_t>(master) | reinterpret_cast<uintptr_t>(grad) |
+                          reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v);
+    if ((all & 15u) != 0) return HTEX_ERR_INVALID_ARG;
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f)) return HTEX_ERR_INVALID_ARG;
+    const double bc1 = 1.0 - std::pow(double(beta1), double(step));
+    const double bc2 = 1.0 - std::pow(double(beta2), double(step));
+    const AdamParams a{master, grad, m, v, static_cast<float*>(t->d_pool), n, beta1, beta2, eps,
+                       float(double(lr) / bc1), float(1.0 / std::sqrt(bc2))};
+    const int64_t want = (n / 4 + 255) / 256 + 1;
+    const unsigned grid = unsigned(std::min<int64_t>(want, int64_t(t->num_sms) * 8));
+    k_adam<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? HTEX_OK : HTEX_ERR_CUDA;
 }
 
 extern "C" htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, int64_t n,

@@ -2,17 +2,18 @@
 
 The lookup is linear in the stored texels, so its gradient is exact and
 cheap: ``htex_lookup_backward`` scatters dL/dvalue times the blend weights
-into a pool-shaped texel gradient.  ``fit`` runs Adam on an FP32 master copy
-of the pool, writing it into the resident textures before every forward
-pass (``htex_textures_write_pool``).  The lookups and their adjoint run in
-libhtex's kernels; the optimiser step is torch's fused Adam.
+into a pool-shaped texel gradient (queries sorted by halfedge range, so the
+scatter-adds stay in L2).  ``fit`` runs Adam on an FP32 master copy of the
+pool with ``htex_textures_adam_step``, which also writes the new values
+into the resident textures and clears the gradient in the same pass.  The
+lookups, their adjoint and the optimiser step all run in libhtex's kernels.
 """
 from __future__ import annotations
 
 import time
 from dataclasses import dataclass, field
 
-from . import Textures, lookup, lookup_backward
+from . import LOOKUP_BIN, Textures, lookup, lookup_backward
 
 
 @dataclass
@@ -37,26 +38,26 @@ def fit(tex: Textures, batches, steps: int = 200, lr: float = 0.05, init=None) -
     if tex.dtype != "f32":
         raise ValueError("fit needs an FP32 asset (the master copy is written as stored values)")
     master = (init.clone() if init is not None else
-              torch.zeros(tex.pool_elements, dtype=torch.float32, device="cuda")).requires_grad_(True)
-    opt = torch.optim.Adam([master], lr=lr, fused=True)
+              torch.zeros(tex.pool_elements, dtype=torch.float32, device="cuda"))
+    grad = torch.zeros_like(master)
+    m = torch.zeros_like(master)
+    v = torch.zeros_like(master)
+    tex.write_pool(master)
     res = FitResult()
+    losses = torch.empty(steps, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for step in range(steps):
-        q, target = batches(step)
-        with torch.no_grad():
-            tex.write_pool(master.detach())
+    with torch.no_grad():
+        for step in range(steps):
+            q, target = batches(step)
             out = lookup(tex, q)
             diff = out - target
             n = diff.numel()
-            res.losses.append(diff.pow(2).sum().item() / n)
-            grad = lookup_backward(tex, q, (2.0 / n) * diff)
-        master.grad = grad
-        opt.step()
-        opt.zero_grad(set_to_none=True)
+            losses[step] = diff.double().pow(2).sum() / n
+            lookup_backward(tex, q, (2.0 / n) * diff, grad_texels=grad, flags=LOOKUP_BIN)
+            tex.adam_step(master, grad, m, v, step + 1, lr)
     torch.cuda.synchronize()
     res.seconds = time.perf_counter() - t0
     res.steps = steps
-    with torch.no_grad():
-        tex.write_pool(master.detach())
+    res.losses = losses.cpu().tolist()
     return res

@@ -113,3 +113,36 @@ def test_sorted_backward_matches_unsorted_and_oracle():
                                                             g[:k].cpu().numpy().astype(np.float64)), 4)
     c = hx.lookup_backward(tex, q[:k], g[:k], flags=hx.LOOKUP_BIN).double().cpu().numpy()
     assert np.abs(c - ref[:c.shape[0]]).max() <= 1e-5 * max(np.abs(ref).max(), 1.0)
+
+
+def test_adam_step_matches_torch_adam():
+    """htex_textures_adam_step against torch.optim.Adam (plain PyTorch, the
+    same hyper-parameters) over five steps of random gradients: the master
+    copy agrees to float rounding, the pool holds the master copy and the
+    gradient is cleared after every step."""
+    fs, fv, V, _ = syn.uv_sphere(slices=8, rings=6, seed=2)
+    mesh = hx.Mesh(fs, fv, V)
+    log2n = (np.arange(mesh.E) % 4).astype(np.int32)
+    tot = int(sum(4 ** int(k) for k in log2n))
+    tex = hx.Textures.upload(mesh, log2n, np.zeros(tot * 3, np.float32), 3, "f32", hx.BUILD_MIPS)
+    n = tex.pool_elements
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(3)
+    start = torch.randn(n, device="cuda", generator=gen)
+    ref = start.clone().requires_grad_(True)
+    opt = torch.optim.Adam([ref], lr=0.01, betas=(0.8, 0.95), eps=1e-6)
+    master, grad = start.clone(), torch.zeros(n, device="cuda")
+    m, v = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    for step in range(1, 6):
+        g = torch.randn(n, device="cuda", generator=gen) * (10.0 ** (step - 3))
+        ref.grad = g.clone()
+        opt.step()
+        grad.copy_(g)
+        tex.adam_step(master, grad, m, v, step, 0.01, betas=(0.8, 0.95), eps=1e-6)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(grad) == 0
+        assert torch.allclose(master, ref.detach(), rtol=1e-5, atol=1e-6)
+        pool = torch.from_numpy(tex.download_pool()[0].view(np.float32).copy()).cuda()
+        assert torch.equal(pool, master)
+    with pytest.raises(hx.HtexError):
+        tex.adam_step(master, grad, m, v, 0, 0.01)

@@ -606,10 +606,14 @@ def frame_bench(hx, torch, stream, mesh, tex, positions, rows):
     raster_ms = timed(torch, stream, lambda: g.rasterize(M, W, H, queries=q, stream=stream), 20)
     lookup_ms = timed(torch, stream, lambda: hx.lookup(tex, q, out=out, stream=stream), 50)
     covered = float((q[:, 0] >= 0).float().mean().item())
+    qa = torch.empty((W * H, 8), dtype=torch.int32, device="cuda")
+    raster_aniso_ms = timed(torch, stream, lambda: g.rasterize_aniso(M, W, H, queries=qa, stream=stream), 20)
+    aniso_ms = timed(torch, stream, lambda: hx.lookup_aniso(tex, qa, 16, out=out, stream=stream), 20)
     g.close()
     return {"width": W, "height": H, "covered_fraction": covered, "raster_ms": raster_ms,
             "lookup_ms": lookup_ms, "frame_ms": raster_ms + lookup_ms,
             "lookups_per_s": W * H * covered / (lookup_ms / 1e3),
+            "aniso16_frame_ms": raster_aniso_ms + aniso_ms, "aniso16_lookup_ms": aniso_ms,
             "context": "the paper's Htex RGB frame (GL tessellation + raster + fragment lookup) took "
                        "0.42 ms on an RTX 3090 for a different asset; not a like-for-like figure"}
 

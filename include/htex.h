@@ -413,6 +413,15 @@ htex_status htex_triangle_vertices(const htex_geometry* g, float* out, htex_stre
 htex_status htex_rasterize(const htex_geometry* g, const float* view_proj, int32_t width, int32_t height,
                            htex_query* queries, float* depth, htex_stream stream);
 
+/* htex_rasterize for anisotropic filtering: the same pixels, triangles and
+ * barycentrics, written as htex_query_aniso (32 bytes, 16-byte aligned)
+ * whose derivatives are the differences of the barycentrics at the centres
+ * one pixel right (du/dx, dv/dx) and one pixel down (du/dy, dv/dy) in the
+ * same triangle; h = -1 and zero derivatives where nothing is seen.  For
+ * htex_lookup_aniso. */
+htex_status htex_rasterize_aniso(const htex_geometry* g, const float* view_proj, int32_t width, int32_t height,
+                                 htex_query_aniso* queries, float* depth, htex_stream stream);
+
 /* Displacement (Section 5.1): for every halfedge triangle the lattice
  * (u, v) = (i/T, j/T), i + j <= T (k = 0.. in order of i, then j), is
  * moved along the interpolated normal of the input mesh (vertex normals at

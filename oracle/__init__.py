@@ -371,7 +371,7 @@ def _project(view_proj, pts):
     return ph @ M.T
 
 
-def rasterize(mesh: Mesh, positions, view_proj, width: int, height: int):
+def rasterize(mesh: Mesh, positions, view_proj, width: int, height: int, derivatives: bool = False):
     """Per pixel centre (x + 1/2, y + 1/2), the intrinsic triangle seen
     first: the triangle whose interior (barycentrics >= 0) contains the
     centre with the smallest depth z/w in [-1, 1]; its perspective-correct
@@ -380,8 +380,10 @@ def rasterize(mesh: Mesh, positions, view_proj, width: int, height: int):
     same triangle's barycentrics at the centres one pixel right and down.
     Returns h [H_px, W_px] (-1 where empty), u, v, footprint, depth, and the
     barycentric margin and depth gap to the runner-up (for deciding which
-    pixels have a unique answer).  Plain loops over pixels, vectorised over
-    triangles: small images only."""
+    pixels have a unique answer).  With 'derivatives', also the differences
+    du/dx, dv/dx, du/dy, dv/dy of the barycentrics at those neighbouring
+    centres (the footprint of an anisotropic lookup).  Plain loops over
+    pixels, vectorised over triangles: small images only."""
     tri = triangle_vertices(mesh, positions)           # v0 = Vert(Next h), v1 = centroid, v2 = Vert(h)
     clip = _project(view_proj, tri)                    # [H][3][4]
     w = clip[..., 3]
@@ -389,7 +391,8 @@ def rasterize(mesh: Mesh, positions, view_proj, width: int, height: int):
     sx = (ndc[..., 0] * 0.5 + 0.5) * width
     sy = (0.5 - ndc[..., 1] * 0.5) * height
     hh = np.full((height, width), -1, np.int64)
-    out = {k: np.full((height, width), np.nan) for k in ("u", "v", "f", "depth", "margin", "gap")}
+    out = {k: np.full((height, width), np.nan)
+           for k in ("u", "v", "f", "depth", "margin", "gap", "dudx", "dvdx", "dudy", "dvdy")}
 
     def bary(px, py):
         # screen-space barycentrics of (px, py) in every triangle, then perspective-corrected
@@ -423,7 +426,12 @@ def rasterize(mesh: Mesh, positions, view_proj, width: int, height: int):
             _, _, ux, vx = bary(x + 1.5, y + 0.5)
             _, _, uy, vy = bary(x + 0.5, y + 1.5)
             out["f"][y, x] = max(np.hypot(ux[k] - u[k], vx[k] - v[k]), np.hypot(uy[k] - u[k], vy[k] - v[k]))
-    return hh, out["u"], out["v"], out["f"], out["depth"], out["margin"], out["gap"]
+            out["dudx"][y, x], out["dvdx"][y, x] = ux[k] - u[k], vx[k] - v[k]
+            out["dudy"][y, x], out["dvdy"][y, x] = uy[k] - u[k], vy[k] - v[k]
+    res = (hh, out["u"], out["v"], out["f"], out["depth"], out["margin"], out["gap"])
+    if derivatives:
+        res += (out["dudx"], out["dvdx"], out["dudy"], out["dvdy"])
+    return res
 
 
 def displace(mesh: Mesh, tex: Textures, positions, tess: int, scale: float, channel: int = 0):

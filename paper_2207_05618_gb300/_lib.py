@@ -67,6 +67,7 @@ _SIGNATURES = {
     "htex_geometry_destroy": ([P], None),
     "htex_triangle_vertices": ([P, P, P], I32),
     "htex_rasterize": ([P, P, I32, I32, P, P, P], I32),
+    "htex_rasterize_aniso": ([P, P, I32, I32, P, P, P], I32),
     "htex_displace": ([P, P, I32, ctypes.c_float, I32, P, P], I32),
     "htex_server_create": ([P, PP], I32),
     "htex_server_add_asset": ([P, P, I32, I32, P, P, P, P], I32),

@@ -19,6 +19,8 @@
 #include <new>
 #include <vector>
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 #include "htex_internal.h"
@@ -148,32 +150,39 @@ __global__ void k_raster(htex_geometry g, Camera cam, unsigned long long* vis) {
     }
 }
 
-__global__ void k_resolve(htex_geometry g, Camera cam, const unsigned long long* vis, htex_query* q, float* depth) {
+// Per pixel: the visible triangle's perspective-correct barycentrics at the
+// pixel centre and at the centres one pixel right and one pixel down; Q is
+// htex_query (footprint = the longer of the two differences) or
+// htex_query_aniso (the two differences as the screen derivatives).
+template <class Q>
+__global__ void k_resolve(htex_geometry g, Camera cam, const unsigned long long* vis, Q* q, float* depth) {
     const int64_t n = int64_t(cam.W) * cam.Ht;
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
         const unsigned long long key = vis[i];
-        htex_query r{-1, 0.0f, 0.0f, 0.0f};
+        int32_t h = -1;
+        float u = 0.0f, vv = 0.0f, ux = 0.0f, vx = 0.0f, uy = 0.0f, vy = 0.0f;
         float zd = __int_as_float(0x7fc00000);
         if (key != ~0ull) {
-            const int32_t h = int32_t(uint32_t(key & 0xffffffffull));
+            h = int32_t(uint32_t(key & 0xffffffffull));
             float3 v[3];
             alg1(g, h, v[0], v[1], v[2]);
             Screen s;
             project(cam, v, s);
             const float px = float(i % cam.W) + 0.5f, py = float(i / cam.W) + 0.5f;
-            float u, vv, ux, vx, uy, vy;
             uv_at(s, px, py, u, vv);
             uv_at(s, px + 1.0f, py, ux, vx);
             uv_at(s, px, py + 1.0f, uy, vy);
-            r.h = h;
-            r.u = u;
-            r.v = vv;
-            r.footprint = fmaxf(hypotf(ux - u, vx - vv), hypotf(uy - u, vy - vv));
             float l0, l1, l2;
             screen_bary(s, px, py, l0, l1, l2);
             zd = l0 * s.z[0] + l1 * s.z[1] + l2 * s.z[2];
         }
-        q[i] = r;
+        if constexpr (std::is_same<Q, htex_query_aniso>::value) {
+            q[i] = h < 0 ? htex_query_aniso{-1, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}
+                         : htex_query_aniso{h, u, vv, 0.0f, ux - u, vx - vv, uy - u, vy - vv};
+        } else {
+            q[i] = h < 0 ? htex_query{-1, 0.0f, 0.0f, 0.0f}
+                         : htex_query{h, u, vv, fmaxf(hypotf(ux - u, vx - vv), hypotf(uy - u, vy - vv))};
+        }
         if (depth) depth[i] = zd;
     }
 }
@@ -322,8 +331,11 @@ extern "C" htex_status htex_triangle_vertices(const htex_geometry* g, float* out
     return cudaGetLastError() == cudaSuccess ? HTEX_OK : HTEX_ERR_CUDA;
 }
 
-extern "C" htex_status htex_rasterize(const htex_geometry* g, const float* view_proj, int32_t width, int32_t height,
-                                      htex_query* queries, float* depth, htex_stream stream) {
+namespace {
+
+template <class Q>
+htex_status rasterize(const htex_geometry* g, const float* view_proj, int32_t width, int32_t height, Q* queries,
+                      float* depth, htex_stream stream) {
     if (!g || !view_proj || !queries || width <= 0 || height <= 0) return HTEX_ERR_INVALID_ARG;
     if (int64_t(width) * height >= (int64_t(1) << 31)) return HTEX_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(queries) & 15u) != 0) return HTEX_ERR_INVALID_ARG;
@@ -345,10 +357,23 @@ extern "C" htex_status htex_rasterize(const htex_geometry* g, const float* view_
     auto* v = static_cast<unsigned long long*>(vis);
     k_clear<<<grid_for(n), kThreads, 0, s>>>(v, n);
     k_raster<<<grid_for(g->H), kThreads, 0, s>>>(*g, cam, v);
-    k_resolve<<<grid_for(n), kThreads, 0, s>>>(*g, cam, v, queries, depth);
+    k_resolve<Q><<<grid_for(n), kThreads, 0, s>>>(*g, cam, v, queries, depth);
     const bool ok = cudaGetLastError() == cudaSuccess;
     cudaFreeAsync(vis, s);
     return ok ? HTEX_OK : HTEX_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" htex_status htex_rasterize(const htex_geometry* g, const float* view_proj, int32_t width, int32_t height,
+                                      htex_query* queries, float* depth, htex_stream stream) {
+    return rasterize(g, view_proj, width, height, queries, depth, stream);
+}
+
+extern "C" htex_status htex_rasterize_aniso(const htex_geometry* g, const float* view_proj, int32_t width,
+                                            int32_t height, htex_query_aniso* queries, float* depth,
+                                            htex_stream stream) {
+    return rasterize(g, view_proj, width, height, queries, depth, stream);
 }
 
 extern "C" htex_status htex_displace(const htex_geometry* g, const htex_textures* t, int32_t tess, float scale,

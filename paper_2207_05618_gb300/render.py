@@ -40,6 +40,19 @@ class Geometry:
               "htex_rasterize")
         return queries
 
+    def rasterize_aniso(self, view_proj, width: int, height: int, queries=None, depth=None, stream=None):
+        """Anisotropic queries (int32 [height * width, 8], CUDA, laid out as
+        htex_query_aniso) and optional depth."""
+        import torch
+        m = np.ascontiguousarray(view_proj, np.float32).reshape(16)
+        if queries is None:
+            queries = torch.empty((width * height, 8), dtype=torch.int32, device="cuda")
+        dptr = ctypes.c_void_p(depth.data_ptr()) if depth is not None else None
+        check(self._lib.htex_rasterize_aniso(self._h, m.ctypes.data_as(ctypes.c_void_p), int(width), int(height),
+                                             ctypes.c_void_p(queries.data_ptr()), dptr, _stream(stream)),
+              "htex_rasterize_aniso")
+        return queries
+
     def displace(self, tex: Textures, tess: int, scale: float, channel: int = 0, stream=None):
         import torch
         K = (tess + 1) * (tess + 2) // 2

@@ -73,6 +73,30 @@ def test_rasterizer_matches_reference(W, H):
             assert c[2] / c[3] <= dref[y, x] + 1e-4
 
 
+@pytest.mark.parametrize("W,H", [(96, 64), (61, 37)])
+def test_anisotropic_rasterizer_matches_reference(W, H):
+    """htex_rasterize_aniso: the same halfedges and barycentrics as
+    htex_rasterize (bit for bit), and on clear pixels the oracle's screen
+    derivatives of the barycentrics; empty pixels carry h = -1."""
+    fs, fv, V, pos = _sphere()
+    mo = oracle.mesh_from_faces(fs, fv, V)
+    M = syn.perspective(40.0, W / H, 0.3, 10.0) @ syn.look_at([2.3, -1.1, 0.9], [0, 0, 0], [0, 0, 1])
+    g = render.Geometry(hx.Mesh(fs, fv, V), pos)
+    qi = g.rasterize(M, W, H).cpu().numpy()
+    qa = g.rasterize_aniso(M, W, H).cpu().numpy()
+    np.testing.assert_array_equal(qa[:, :3], qi[:, :3])
+    pos32 = pos.astype(np.float32).astype(np.float64)
+    r = oracle.rasterize(mo, pos32, M.astype(np.float32).astype(np.float64), W, H, derivatives=True)
+    hh, margin, gap = r[0], r[5], r[6]
+    clear = (hh >= 0) & (margin > 1e-4) & (gap > 1e-4)
+    assert clear.sum() > 0
+    for col, ref in zip(range(4, 8), r[7:11]):
+        got = qa[:, col].copy().view(np.float32).reshape(H, W)
+        np.testing.assert_allclose(got[clear], ref[clear], rtol=2e-3, atol=2e-6)
+    empty = qa[:, 0] < 0
+    assert np.all(qa[empty][:, 4:] == 0)
+
+
 def test_frame_pipeline_full_hd():
     """1920x1080 frame of the closed sphere filling the view: every pixel
     inside the silhouette gets a valid query, the lookup returns finite

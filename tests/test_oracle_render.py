@@ -110,3 +110,27 @@ def test_displacement_is_crack_free_with_corner_preprocessing():
     P2 = oracle.displace(m, t2, pos, T, 0.3).reshape(-1, 3)
     spread = max(np.abs(P2[inv == g] - P2[inv == g][0]).max() for g in np.unique(inv[shared]))
     assert spread > 1e-3
+
+
+def test_rasterizer_derivatives_project_to_neighbour_pixels():
+    """The derivatives are differences of the same triangle's barycentrics
+    at the centres one pixel right and one pixel down: the surface points at
+    (u + du/dx, v + dv/dx) and (u + du/dy, v + dv/dy) project onto those
+    centres, and the isotropic footprint is the longer of the two."""
+    fs, fv, V, pos = syn.cube()
+    m = oracle.mesh_from_faces(fs, fv, V)
+    W, H = 32, 24
+    M = _camera(W, H)
+    hh, u, v, f, depth, margin, gap, dudx, dvdx, dudy, dvdy = oracle.rasterize(m, pos, M, W, H, derivatives=True)
+    tri = oracle.triangle_vertices(m, pos)
+    covered = np.argwhere(hh >= 0)
+    assert len(covered) > 0.2 * W * H
+    for y, x in covered:
+        k = hh[y, x]
+        for du, dv, ex, ey in ((dudx[y, x], dvdx[y, x], x + 1.5, y + 0.5), (dudy[y, x], dvdy[y, x], x + 0.5, y + 1.5)):
+            uu, vv = u[y, x] + du, v[y, x] + dv
+            P = uu * tri[k, 2] + vv * tri[k, 0] + (1 - uu - vv) * tri[k, 1]
+            c = M @ np.append(P, 1.0)
+            assert abs((c[0] / c[3] * 0.5 + 0.5) * W - ex) < 1e-9
+            assert abs((0.5 - c[1] / c[3] * 0.5) * H - ey) < 1e-9
+        assert f[y, x] == max(np.hypot(dudx[y, x], dvdx[y, x]), np.hypot(dudy[y, x], dvdy[y, x]))

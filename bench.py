@@ -91,6 +91,11 @@ def workload_config(H, E, nq, flags_name):
     }
 
 
+def arm_flags_name(args) -> str:
+    return ("none" if args.no_bin else
+            "sorted by halfedge range (htex_queries_sort, htex_lookup, htex_results_gather)")
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_2207_05618_gb300", "csrc", "*"))):
@@ -301,7 +306,8 @@ def run_reference(args, rank):
         oracle.lookup(mo, to, sub, nthreads=cores)
     dt = time.perf_counter() - t
     value = n * args.steps / dt
-    cfg = workload_config(mo.H, mo.num_edges, n, "oracle")
+    # the same config object as this bench's own arm; the bounded sample is described in cpu_baseline
+    cfg = workload_config(mo.H, mo.num_edges, args.queries, arm_flags_name(args))
     sample = (f"{n} queries per step with h uniform on halfedges [0, 4096) of the asset, "
               f"barycentrics and footprints as the workload; FP64 oracle on {cores} host threads")
     print(json.dumps({
@@ -460,8 +466,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(mesh.H, mesh.E, nq, "sorted by halfedge range (htex_queries_sort, "
-                                      "htex_lookup, htex_results_gather)" if use_bin else "none"),
+            "config": workload_config(mesh.H, mesh.E, nq, arm_flags_name(args)),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * launches_per_step, "step_ms_stages": stages,
             "cube_stream": cube, "serving": serving,

@@ -1,14 +1,17 @@
 // Forward filtered lookup (paper Section 4.4, Alg. 3 with Alg. 2), query
 // binning, and the htex_lookup entry point.
 //
-// One thread per query in a grid-stride loop over a persistent grid, with
-// the next query's load issued before the current one is filtered.  Per
+// One thread per query in a grid-stride loop over a persistent grid.  Per
 // query: one streaming 16-byte query load, one 16-byte packed record
 // (edges and Alg. 2 reflections of h, Next(h), Prev(h)), then up to three
 // fetches, each one or two levels of 2x2 border-aware taps; a fetch whose
 // taps all fall outside its texture loads nothing.  Two memory paths: the
-// pool staged in shared memory (small assets, many queries) or gathered
-// through the read-only cache from global memory.
+// pool gathered through the read-only cache from global memory (queries
+// two iterations and records one iteration ahead in flight), or staged in
+// shared memory for small assets and many queries (two queries per thread
+// and iteration).  Both come in a variant for assets whose textures share
+// one resolution, which keeps everything derived from it warp-uniform, and
+// use 32-bit indices when the query count allows.
 //
 // Binning (HTEX_LOOKUP_BIN), for pools well beyond L2: the queries are
 // counting-sorted into 128 ranges of consecutive halfedges, in chunks of

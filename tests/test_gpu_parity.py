@@ -159,6 +159,39 @@ def test_empty_and_single_query():
     _cmp(_gpu(tl, qs), oracle.lookup(mo, to, qs))
 
 
+@pytest.mark.parametrize("top,C,fmt", [(13, 1, "u8"), (12, 4, "f32")])
+def test_maximum_resolution_texture(top, C, fmt):
+    """One texture at the top resolution (8192^2 is the cap), the others
+    small, footprints spanning every level of it (2^-15 .. 2): 32-bit
+    texel offsets reach the top of the chain, and the result matches the
+    oracle; also the sorted step and the anisotropic lookup."""
+    fs, fv, V, _ = syn.cube()
+    mo = oracle.mesh_from_faces(fs, fv, V)
+    ml = hx.Mesh(fs, fv, V)
+    log2n = (np.arange(mo.num_edges) % 4).astype(np.int32)
+    log2n[5] = top
+    tex = (syn.texels_u8 if fmt == "u8" else syn.texels_f32)(log2n, C, seed=31)
+    to = oracle.prepare_textures(mo, log2n, tex, C, fmt, hx.BUILD_MIPS)
+    tl = hx.Textures.upload(ml, log2n, tex, C, fmt, hx.BUILD_MIPS)
+    hs = np.array([h for h in range(mo.H) if mo.edge[h] == 5 or mo.edge[mo.next[h]] == 5
+                   or mo.edge[mo.prev[h]] == 5], np.int32)
+    n = 200003
+    _, u, v, f = syn.queries(mo.H, n, seed=32, footprint="loguniform", lo=-15, hi=1)
+    h = np.random.default_rng(33).choice(hs, n).astype(np.int32)
+    qs = (h, u, v, f)
+    ref = oracle.lookup(mo, to, qs, nthreads=8)
+    got = _gpu(tl, qs)
+    _cmp(got, ref)
+    q = torch.from_numpy(hx.pack_queries(*qs)).cuda()
+    sq, pos = hx.sort_queries(tl, q)
+    np.testing.assert_array_equal(hx.gather_results(hx.lookup(tl, sq), pos).cpu().numpy().astype(np.float64), got)
+    rng = np.random.default_rng(34)
+    d = [np.float32(x) for x in rng.uniform(-1e-3, 1e-3, (4, 20000))]
+    qa = (h[:20000], u[:20000], v[:20000], *d)
+    a = hx.lookup_aniso(tl, torch.from_numpy(hx.pack_queries_aniso(*qa)).cuda(), 16).cpu().numpy()
+    _cmp(a.astype(np.float64), oracle.lookup_aniso(mo, to, qa, 16, nthreads=8), 4.6e-5)
+
+
 def test_pool_round_trip_matches_host_preparation():
     fs, fv, V, _ = syn.cylinder(around=12, rows=5, seed=1)
     ml = hx.Mesh(fs, fv, V)

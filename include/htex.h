@@ -486,7 +486,11 @@ htex_status htex_server_add_asset(htex_server* s, const htex_mesh* m, int32_t ch
                                   int32_t* asset_id);
 
 /* Queue n queries (host) against an asset; results go to out (host,
- * [n][channels] float).  Returns at once with the request's id. */
+ * [n][channels] float).  Returns at once with the request's id.  When q
+ * and out are page-locked, mapped into the device's address space and
+ * 16-byte aligned, the batches read and write them in place; otherwise
+ * they are copied through the server's device staging.  Either way the
+ * buffers must stay valid until the request completes. */
 htex_status htex_server_submit(htex_server* s, int32_t asset_id, const htex_query* q, int64_t n,
                                float* out, int64_t* request_id);
 

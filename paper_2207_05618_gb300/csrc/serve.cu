@@ -14,7 +14,10 @@
 //   4. launches the batch: query copies in, the slot's graph (a memcpy node
 //      for the batch's descriptor table, then one persistent kernel per
 //      texel format whose blocks pull 4096-query tiles of any item through
-//      an atomic counter), result copies out, a completion event.
+//      an atomic counter), result copies out, a completion event.  A
+//      request whose buffers are page-locked, mapped into the device's
+//      address space and 16-byte aligned skips both copies: its items point
+//      the kernel at the host buffers themselves.
 // Every query is computed by the same per-query code as htex_lookup, so a
 // request's results do not depend on what else shares its batches.
 #include <algorithm>
@@ -135,6 +138,8 @@ struct Request {
     int32_t asset = 0;
     const htex_query* q = nullptr;
     float* out = nullptr;
+    const htex_query* dq = nullptr;   // device addresses of mapped host buffers,
+    float* dout = nullptr;            // or null: staged through the slot's buffers
     int64_t n = 0, issued = 0, done = 0;
     Clock::time_point t_submit;
     bool active = false;
@@ -372,19 +377,21 @@ bool launch_batch(htex_server* s, Slot& sl) {
         d.hdr = static_cast<const uint8_t*>(t->d_hdr);
         d.scale = static_cast<const uint8_t*>(t->d_scale);
         d.pool = static_cast<const uint8_t*>(t->d_pool);
-        d.q = sl.d_q + qoff;
-        d.out = sl.d_out + ooff;
+        d.q = r->dq ? r->dq + r->issued : sl.d_q + qoff;
+        d.out = r->dout ? r->dout + r->issued * t->C : sl.d_out + ooff;
         d.H = t->H;
         d.uniform_log2n = t->uniform_log2n;
         d.uniform_stride16 = uint32_t(t->uniform_stride / 16);
         d.n = int32_t(c);
-        if (cudaMemcpyAsync(sl.d_q + qoff, r->q + r->issued, size_t(c) * sizeof(htex_query), cudaMemcpyHostToDevice,
-                            sl.stream) != cudaSuccess) {
-            fail(s, HTEX_ERR_CUDA);
-            return false;
+        if (!r->dq) {
+            if (cudaMemcpyAsync(sl.d_q + qoff, r->q + r->issued, size_t(c) * sizeof(htex_query),
+                                cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) {
+                fail(s, HTEX_ERR_CUDA);
+                return false;
+            }
+            qoff += c;
         }
-        qoff += c;
-        ooff += c * t->C;
+        if (!r->dout) ooff += c * t->C;
         a->last_use = ++s->tick;
     }
     if (cudaGraphLaunch(sl.exec, sl.stream) != cudaSuccess) {
@@ -396,12 +403,14 @@ bool launch_batch(htex_server* s, Slot& sl) {
         Request* r = take[k].first;
         const int64_t c = take[k].second;
         const int C = s->assets[r->asset]->tex->C;
-        if (cudaMemcpyAsync(r->out + r->issued * C, sl.d_out + ooff, size_t(c) * C * sizeof(float),
-                            cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess) {
-            fail(s, HTEX_ERR_CUDA);
-            return false;
+        if (!r->dout) {
+            if (cudaMemcpyAsync(r->out + r->issued * C, sl.d_out + ooff, size_t(c) * C * sizeof(float),
+                                cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess) {
+                fail(s, HTEX_ERR_CUDA);
+                return false;
+            }
+            ooff += c * C;
         }
-        ooff += c * C;
         r->issued += c;
         sl.items.push_back({r, c});
     }
@@ -595,6 +604,16 @@ extern "C" htex_status htex_server_add_asset(htex_server* s, const htex_mesh* m,
     return HTEX_OK;
 }
 
+// Device address of a page-locked, mapped host buffer, else null.
+static const void* mapped_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 extern "C" htex_status htex_server_submit(htex_server* s, int32_t asset_id, const htex_query* q, int64_t n,
                                           float* out, int64_t* request_id) {
     if (!s || !request_id || n < 0 || n >= (int64_t(1) << 40)) return HTEX_ERR_INVALID_ARG;
@@ -605,6 +624,14 @@ extern "C" htex_status htex_server_submit(htex_server* s, int32_t asset_id, cons
     r->q = q;
     r->out = out;
     r->n = n;
+    if (n > 0) {
+        const void* mq = mapped_host(q);
+        void* mo = const_cast<void*>(mapped_host(out));
+        if (mq && mo && ((reinterpret_cast<uintptr_t>(mq) | reinterpret_cast<uintptr_t>(mo)) & 15u) == 0) {
+            r->dq = static_cast<const htex_query*>(mq);
+            r->dout = static_cast<float*>(mo);
+        }
+    }
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> g(s->mu);
     if (s->error != HTEX_OK) {

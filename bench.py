@@ -105,16 +105,29 @@ def source_hash() -> str:
     return h.hexdigest()[:12]
 
 
+# the files the filter kernel is compiled from (and the build flags)
+FILTER_SOURCES = ("csrc/lookup.cu", "csrc/lookup_core.cuh", "csrc/fetch.cuh", "csrc/htex_internal.h", "build.py")
+
+
+def filter_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in FILTER_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_05618_gb300", rel), "rb") as fh:
+            h.update(rel.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def profiled_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, when it was
-    taken on the current kernel sources; else None."""
+    taken on the filter kernel's current sources; else None."""
     path = os.path.join(ROOT, "profiles", "lookup_asset_scale.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    m = re.search(r"filter_source_hash:\s*([0-9a-f]+)", text)
     t = re.search(rf"{kernel}_dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if m and t and m.group(1) == source_hash():
+    if m and t and m.group(1) == filter_source_hash():
         return float(t.group(1))
     return None
 

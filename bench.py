@@ -106,7 +106,8 @@ def source_hash() -> str:
 
 
 # the files the filter kernel is compiled from (and the build flags)
-FILTER_SOURCES = ("csrc/lookup.cu", "csrc/lookup_core.cuh", "csrc/fetch.cuh", "csrc/htex_internal.h", "build.py")
+FILTER_SOURCES = ("csrc/lookup_kernels.cuh", "csrc/lookup_u8.cu", "csrc/lookup_core.cuh", "csrc/fetch.cuh",
+                  "csrc/htex_internal.h", "build.py")
 
 
 def filter_source_hash() -> str:
@@ -460,7 +461,7 @@ def main():
     achieved = bytes_per_lookup * nq / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic("lookup"), "peak_source": peak_src,
-                "algorithmic_bytes_per_lookup": bytes_per_lookup, "kernel": "k_lookup_global<u8,4>",
+                "algorithmic_bytes_per_lookup": bytes_per_lookup, "kernel": "k_lookup_global<u8,4> (lookup_u8.cu)",
                 "avg_launch_ms": avg_ms}
 
     cpu = None

@@ -1,0 +1,11 @@
+// Filter kernels of htex_lookup for bf16 texels (one translation unit
+// per texel format, compiled in parallel).
+#include "lookup_kernels.cuh"
+
+namespace htex {
+
+htex_status launch_fwd_bf16(const htex_textures* t, const FwdParams& p, uint32_t flags, cudaStream_t s, bool binned) {
+    return binned ? launch_fwd_c<HTEX_BF16, true>(t, p, flags, s) : launch_fwd_c<HTEX_BF16, false>(t, p, flags, s);
+}
+
+}  // namespace htex

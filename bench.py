@@ -685,16 +685,12 @@ def aniso_bench(hx, torch, stream, mesh, tex, n=1 << 22):
     out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
     for _ in range(3):
         hx.lookup_aniso(tex, q, 16, out=out, stream=stream)
-    reps = 10
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        hx.lookup_aniso(tex, q, 16, out=out, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+    ms = timed(torch, stream, lambda: hx.lookup_aniso(tex, q, 16, out=out, stream=stream), 10)
+    sorted_ms = timed(torch, stream, lambda: hx.lookup_aniso(tex, q, 16, out=out, stream=stream,
+                                                             flags=hx.LOOKUP_BIN), 10)
     return {"queries": n, "max_aniso": 16, "mean_probes": float(k.mean()), "ms": ms,
-            "lookups_per_s": n / (ms / 1e3), "probes_per_s": float(k.sum()) / (ms / 1e3)}
+            "lookups_per_s": n / (ms / 1e3), "probes_per_s": float(k.sum()) / (ms / 1e3),
+            "sorted_ms": sorted_ms, "sorted_lookups_per_s": n / (sorted_ms / 1e3)}
 
 
 def backward_bench(hx, torch, stream):

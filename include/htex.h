@@ -277,13 +277,16 @@ htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, 
  *   placed.
  *   q          device [n] htex_query_aniso (16-byte aligned)
  *   max_aniso  1..16
+ *   flags      HTEX_LOOKUP_BIN: sort the queries by halfedge range first,
+ *              as htex_lookup does (same results; scratch of 36 + 4 *
+ *              channels bytes per chunk query)
  *   out        device [n][channels] float (alignment as htex_lookup)
  *   d_status   device int32, nullable: incremented once per invalid query
  *              (h out of range, non-finite u, v or derivative, or an
  *              overflowing squared length); such a query gives NaN.
  * FP32 accumulation over at most 24 * max_aniso taps.  Asynchronous. */
 htex_status htex_lookup_aniso(const htex_textures* t, const htex_query_aniso* q, int64_t n, int32_t max_aniso,
-                              float* out, htex_stream stream, int32_t* d_status);
+                              uint32_t flags, float* out, htex_stream stream, int32_t* d_status);
 
 /* The two halves of HTEX_LOOKUP_BIN as calls of their own, for callers
  * that filter one sorted batch more than once (several texture sets on

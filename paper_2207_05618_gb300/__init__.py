@@ -253,8 +253,9 @@ def pack_queries_aniso(h, u, v, dudx, dvdx, dudy, dvdy) -> np.ndarray:
     return np.ascontiguousarray(np.stack([h, cols[0], cols[1], np.zeros_like(h)] + d, 1))
 
 
-def lookup_aniso(tex: Textures, queries, max_aniso: int = 16, out=None, stream=None, status=None):
-    """htex_lookup_aniso: queries int32 CUDA tensor [n, 8] -> float32 [n, channels]."""
+def lookup_aniso(tex: Textures, queries, max_aniso: int = 16, out=None, stream=None, status=None, flags: int = 0):
+    """htex_lookup_aniso: queries int32 CUDA tensor [n, 8] -> float32 [n, channels]
+    (flags: LOOKUP_BIN sorts the queries by halfedge range first)."""
     import torch
     _check_tensor(queries, "queries", torch.int32, 8)
     n = queries.shape[0]
@@ -263,7 +264,7 @@ def lookup_aniso(tex: Textures, queries, max_aniso: int = 16, out=None, stream=N
     else:
         _check_tensor(out, "out", torch.float32, tex.channels)
     st = ctypes.c_void_p(status.data_ptr()) if status is not None else None
-    check(tex._lib.htex_lookup_aniso(tex._h, ctypes.c_void_p(queries.data_ptr()), n, int(max_aniso),
+    check(tex._lib.htex_lookup_aniso(tex._h, ctypes.c_void_p(queries.data_ptr()), n, int(max_aniso), int(flags),
                                      ctypes.c_void_p(out.data_ptr()), _stream(stream), st), "htex_lookup_aniso")
     return out
 

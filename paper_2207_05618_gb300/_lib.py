@@ -56,7 +56,7 @@ _SIGNATURES = {
     "htex_textures_write_pool": ([P, I64, I64, P, P], I32),
     "htex_textures_destroy": ([P], None),
     "htex_lookup": ([P, P, I64, P, U32, P, P], I32),
-    "htex_lookup_aniso": ([P, P, I64, I32, P, P, P], I32),
+    "htex_lookup_aniso": ([P, P, I64, I32, U32, P, P, P], I32),
     "htex_queries_sort": ([P, P, I64, P, P, P], I32),
     "htex_results_gather": ([P, P, I64, I32, P, P], I32),
     "htex_lookup_backward": ([P, P, I64, P, P, U32, P, P], I32),

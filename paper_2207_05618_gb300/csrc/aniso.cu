@@ -177,15 +177,9 @@ htex_status launch_aniso_dt(const htex_textures* t, const AnisoParams& p, cudaSt
 
 using namespace htex;
 
-extern "C" htex_status htex_lookup_aniso(const htex_textures* t, const htex_query_aniso* q, int64_t n,
-                                         int32_t max_aniso, float* out, htex_stream stream, int32_t* d_status) {
-    if (!t || n < 0 || max_aniso < 1 || max_aniso > 16) return HTEX_ERR_INVALID_ARG;
-    if (n == 0) return HTEX_OK;
-    if (!q || !out) return HTEX_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(q) & 15u) != 0) return HTEX_ERR_INVALID_ARG;
-    const uintptr_t out_align = t->C == 4 ? 16u : (t->C == 2 ? 8u : 4u);
-    if ((reinterpret_cast<uintptr_t>(out) & (out_align - 1)) != 0) return HTEX_ERR_INVALID_ARG;
-    const AnisoParams p{q, n, max_aniso, out, d_status};
+htex_status htex_launch_aniso(const htex_textures* t, const htex_query_aniso* q, int64_t n, int32_t kmax,
+                              float* out, htex_stream stream, int32_t* d_status) {
+    const AnisoParams p{q, n, kmax, out, d_status};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     switch (t->dtype) {
     case HTEX_F32: return launch_aniso_dt<HTEX_F32>(t, p, s);
@@ -195,4 +189,18 @@ extern "C" htex_status htex_lookup_aniso(const htex_textures* t, const htex_quer
     case HTEX_E4M3: return launch_aniso_dt<HTEX_E4M3>(t, p, s);
     }
     return HTEX_ERR_INVALID_ARG;
+}
+
+extern "C" htex_status htex_lookup_aniso(const htex_textures* t, const htex_query_aniso* q, int64_t n,
+                                         int32_t max_aniso, uint32_t flags, float* out, htex_stream stream,
+                                         int32_t* d_status) {
+    if (!t || n < 0 || max_aniso < 1 || max_aniso > 16) return HTEX_ERR_INVALID_ARG;
+    if (flags & ~uint32_t(HTEX_LOOKUP_BIN)) return HTEX_ERR_INVALID_ARG;
+    if (n == 0) return HTEX_OK;
+    if (!q || !out) return HTEX_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(q) & 15u) != 0) return HTEX_ERR_INVALID_ARG;
+    const uintptr_t out_align = t->C == 4 ? 16u : (t->C == 2 ? 8u : 4u);
+    if ((reinterpret_cast<uintptr_t>(out) & (out_align - 1)) != 0) return HTEX_ERR_INVALID_ARG;
+    if (flags & HTEX_LOOKUP_BIN) return htex_launch_aniso_sorted(t, q, n, max_aniso, out, stream, d_status);
+    return htex_launch_aniso(t, q, n, max_aniso, out, stream, d_status);
 }

@@ -140,20 +140,24 @@ constexpr int kSortPer = 8;
 constexpr int kSortTile = kSortThreads * kSortPer;
 constexpr int kSortMaxBuckets = 512 + 2;   // keeps the scatter's static shared memory under 48 KiB
 
-__global__ void __launch_bounds__(kSortThreads) k_chunk_count(const htex_query* q, int64_t m, int32_t H, int shift,
+// QW: 16-byte words per query (1: htex_query, 2: htex_query_aniso); the
+// halfedge id is the first word's first int.
+template <int QW>
+__global__ void __launch_bounds__(kSortThreads) k_chunk_count(const int4* q, int64_t m, int32_t H, int shift,
                                                               uint32_t B, uint32_t* counts) {
+    constexpr int PER = kSortPer / QW, TILE = kSortThreads * PER;
     __shared__ uint32_t hist[kSortMaxBuckets];
     for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    for (int64_t t0 = int64_t(blockIdx.x) * kSortTile; t0 < m; t0 += int64_t(gridDim.x) * kSortTile) {
-        int32_t h[kSortPer];
+    for (int64_t t0 = int64_t(blockIdx.x) * TILE; t0 < m; t0 += int64_t(gridDim.x) * TILE) {
+        int32_t h[PER];
 #pragma unroll
-        for (int k = 0; k < kSortPer; ++k) {
+        for (int k = 0; k < PER; ++k) {
             const int64_t i = t0 + int64_t(k) * kSortThreads + threadIdx.x;
-            h[k] = i < m ? __ldg(reinterpret_cast<const int32_t*>(q + i)) : 0;
+            h[k] = i < m ? __ldg(reinterpret_cast<const int32_t*>(q + i * QW)) : 0;
         }
 #pragma unroll
-        for (int k = 0; k < kSortPer; ++k)
+        for (int k = 0; k < PER; ++k)
             if (t0 + int64_t(k) * kSortThreads + threadIdx.x < m) atomicAdd(&hist[bucket_of(h[k], H, shift, B - 1)], 1u);
     }
     __syncthreads();
@@ -187,11 +191,13 @@ __device__ __forceinline__ void block_scan_buckets(const uint32_t* x, uint32_t* 
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const htex_query* q, int64_t m, int32_t H, int shift,
+template <int QW>
+__global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const int4* q, int64_t m, int32_t H, int shift,
                                                                 uint32_t B, const uint32_t* counts, uint32_t* taken,
-                                                                htex_query* sq, int32_t* pos, int32_t pos_base) {
-    __shared__ int4 tile[kSortTile];
-    __shared__ uint16_t tile_bucket[kSortTile];
+                                                                int4* sq, int32_t* pos, int32_t pos_base) {
+    constexpr int PER = kSortPer / QW, TILE = kSortThreads * PER;
+    __shared__ int4 tile[TILE * QW];
+    __shared__ uint16_t tile_bucket[TILE];
     __shared__ uint32_t start[kSortMaxBuckets];    // first sorted position of each bucket
     __shared__ uint32_t cnt[kSortMaxBuckets];      // the tile's bucket sizes
     __shared__ uint32_t loff[kSortMaxBuckets];     // the tile's local bucket offsets
@@ -201,21 +207,23 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const htex_query
     __syncthreads();
     block_scan_buckets(cnt, start, B, warp_tot);
 
-    for (int64_t t0 = int64_t(blockIdx.x) * kSortTile; t0 < m; t0 += int64_t(gridDim.x) * kSortTile) {
-        const int tm = int(min(int64_t(kSortTile), m - t0));
+    for (int64_t t0 = int64_t(blockIdx.x) * TILE; t0 < m; t0 += int64_t(gridDim.x) * TILE) {
+        const int tm = int(min(int64_t(TILE), m - t0));
         for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0;
         __syncthreads();
-        int4 r[kSortPer];
-        uint32_t bk[kSortPer], rank[kSortPer];
+        int4 r[PER][QW];
+        uint32_t bk[PER], rank[PER];
 #pragma unroll
-        for (int k = 0; k < kSortPer; ++k) {
+        for (int k = 0; k < PER; ++k) {
             const int j = k * kSortThreads + threadIdx.x;
-            if (j < tm) r[k] = __ldcs(reinterpret_cast<const int4*>(q + t0) + j);
+#pragma unroll
+            for (int w = 0; w < QW; ++w)
+                if (j < tm) r[k][w] = __ldcs(q + (t0 + j) * QW + w);
         }
 #pragma unroll
-        for (int k = 0; k < kSortPer; ++k) {
+        for (int k = 0; k < PER; ++k) {
             if (k * kSortThreads + int(threadIdx.x) < tm) {
-                bk[k] = bucket_of(r[k].x, H, shift, B - 1);
+                bk[k] = bucket_of(r[k][0].x, H, shift, B - 1);
                 rank[k] = atomicAdd(&cnt[bk[k]], 1u);
             }
         }
@@ -225,19 +233,21 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const htex_query
             if (cnt[b]) gbase[b] = start[b] + atomicAdd(&taken[b], cnt[b]);
         __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kSortPer; ++k) {
+        for (int k = 0; k < PER; ++k) {
             const int j = k * kSortThreads + threadIdx.x;
             if (j < tm) {
                 const uint32_t lp = loff[bk[k]] + rank[k];
-                tile[lp] = r[k];
+#pragma unroll
+                for (int w = 0; w < QW; ++w) tile[lp * QW + w] = r[k][w];
                 tile_bucket[lp] = uint16_t(bk[k]);
                 __stcs(pos + t0 + j, pos_base + int32_t(gbase[bk[k]] + rank[k]));
             }
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < tm; j += kSortThreads) {
+        for (int x = threadIdx.x; x < tm * QW; x += kSortThreads) {   // one 16-byte word per thread
+            const int j = x / QW, w = x - j * QW;
             const uint32_t b = tile_bucket[j];
-            reinterpret_cast<int4*>(sq)[gbase[b] + (uint32_t(j) - loff[b])] = tile[j];
+            sq[int64_t(gbase[b] + (uint32_t(j) - loff[b])) * QW + w] = tile[x];
         }
         __syncthreads();
     }
@@ -374,22 +384,27 @@ size_t counter_bytes(const SortPlan& P) { return (size_t(2 * P.B) * 4 + 255) & ~
 
 // Sorts q[0..m) into sq within consecutive chunks of kSortChunk queries;
 // pos[i] = pos_base + where query i went.  counters: counter_bytes(P) of
-// scratch.
-htex_status launch_sort(const htex_textures* t, const SortPlan& P, const htex_query* q, int64_t m,
-                        uint32_t* counters, htex_query* sq, int32_t* pos, int32_t pos_base, cudaStream_t s) {
-    const int64_t blocks = int64_t(t->num_sms) * resident_blocks(k_chunk_scatter, kSortThreads, 0);
+// scratch.  QW: 16-byte words per query.
+template <int QW>
+htex_status launch_sort(const htex_textures* t, const SortPlan& P, const int4* q, int64_t m, uint32_t* counters,
+                        int4* sq, int32_t* pos, int32_t pos_base, cudaStream_t s) {
+    constexpr int64_t TILE = int64_t(kSortThreads) * (kSortPer / QW);
+    const int64_t blocks = int64_t(t->num_sms) * resident_blocks(k_chunk_scatter<QW>, kSortThreads, 0);
     for (int64_t c0 = 0; c0 < m; c0 += kSortChunk) {
         const int64_t mc = std::min<int64_t>(kSortChunk, m - c0);
-        const int64_t g = std::min<int64_t>((mc + kSortTile - 1) / kSortTile, blocks);
+        const int64_t g = std::min<int64_t>((mc + TILE - 1) / TILE, blocks);
         if (cudaMemsetAsync(counters, 0, size_t(2 * P.B) * 4, s) != cudaSuccess) return HTEX_ERR_CUDA;
-        k_chunk_count<<<unsigned(g), kSortThreads, 0, s>>>(q + c0, mc, t->H, P.shift, P.B, counters);
-        k_chunk_scatter<<<unsigned(g), kSortThreads, 0, s>>>(q + c0, mc, t->H, P.shift, P.B, counters,
-                                                             counters + P.B, sq + c0, pos + c0,
-                                                             pos_base + int32_t(c0));
+        k_chunk_count<QW><<<unsigned(g), kSortThreads, 0, s>>>(q + c0 * QW, mc, t->H, P.shift, P.B, counters);
+        k_chunk_scatter<QW><<<unsigned(g), kSortThreads, 0, s>>>(q + c0 * QW, mc, t->H, P.shift, P.B, counters,
+                                                                 counters + P.B, sq + c0 * QW, pos + c0,
+                                                                 pos_base + int32_t(c0));
         if (cudaGetLastError() != cudaSuccess) return HTEX_ERR_CUDA;
     }
     return HTEX_OK;
 }
+
+inline const int4* words(const htex_query* q) { return reinterpret_cast<const int4*>(q); }
+inline int4* words(htex_query* q) { return reinterpret_cast<int4*>(q); }
 
 // Gathers the results of a chunk back into query order.  Positions are
 // relative to the sorted chunk.
@@ -446,7 +461,7 @@ htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int6
     htex_status st = HTEX_OK;
     for (int64_t c0 = 0; c0 < n && st == HTEX_OK; c0 += M) {
         const int64_t m = std::min<int64_t>(M, n - c0);
-        st = launch_sort(t, P, q + c0, m, counters, sq, pos, 0, s);
+        st = launch_sort<1>(t, P, words(q + c0), m, counters, words(sq), pos, 0, s);
         if (st == HTEX_OK) st = launch_fwd_dt<false>(t, FwdParams{sq, m, sout, d_status, nullptr}, fwd_flags, s);
         if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, t->num_sms, s);
     }
@@ -480,7 +495,7 @@ htex_status htex_launch_backward_sorted(const htex_textures* t, const htex_query
     htex_status st = HTEX_OK;
     for (int64_t c0 = 0; c0 < n && st == HTEX_OK; c0 += M) {
         const int64_t m = std::min<int64_t>(M, n - c0);
-        st = launch_sort(t, P, q + c0, m, counters, sq, pos, 0, s);
+        st = launch_sort<1>(t, P, words(q + c0), m, counters, words(sq), pos, 0, s);
         if (st != HTEX_OK) break;
         const float* gsrc = grad_out + c0 * t->C;
         switch (t->C) {
@@ -494,6 +509,39 @@ htex_status htex_launch_backward_sorted(const htex_textures* t, const htex_query
             break;
         }
         st = htex_launch_backward(t, sq, m, gs, grad_texels, 0u, stream, d_status);
+    }
+    cudaFreeAsync(scratch, s);
+    return st;
+}
+
+htex_status htex_launch_aniso_sorted(const htex_textures* t, const htex_query_aniso* q, int64_t n, int32_t kmax,
+                                     float* out, htex_stream stream, int32_t* d_status) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (htex_bin_shift(t) < 0) return htex_launch_aniso(t, q, n, kmax, out, stream, d_status);
+    const SortPlan P = sort_plan(t->H);
+    const int64_t M = std::min<int64_t>(n, kSortChunk);
+    const size_t cnt_b = counter_bytes(P);
+    const size_t sq_b = size_t(M) * sizeof(htex_query_aniso), pos_b = (size_t(M) * 4 + 255) & ~size_t(255);
+    const size_t sout_b = size_t(M) * 4 * size_t(t->C);
+    cudaMemPool_t pool = scratch_pool(t->device);
+    if (!pool) return HTEX_ERR_CUDA;
+    void* scratch = nullptr;
+    if (cudaMallocFromPoolAsync(&scratch, cnt_b + sq_b + pos_b + sout_b, pool, s) != cudaSuccess) {
+        cudaGetLastError();
+        return HTEX_ERR_OUT_OF_MEMORY;
+    }
+    uint8_t* base = static_cast<uint8_t*>(scratch);
+    uint32_t* counters = reinterpret_cast<uint32_t*>(base);
+    htex_query_aniso* sq = reinterpret_cast<htex_query_aniso*>(base + cnt_b);
+    int32_t* pos = reinterpret_cast<int32_t*>(base + cnt_b + sq_b);
+    float* sout = reinterpret_cast<float*>(base + cnt_b + sq_b + pos_b);
+    htex_status st = HTEX_OK;
+    for (int64_t c0 = 0; c0 < n && st == HTEX_OK; c0 += M) {
+        const int64_t m = std::min<int64_t>(M, n - c0);
+        st = launch_sort<2>(t, P, reinterpret_cast<const int4*>(q + c0), m, counters, reinterpret_cast<int4*>(sq),
+                            pos, 0, s);
+        if (st == HTEX_OK) st = htex_launch_aniso(t, sq, m, kmax, sout, stream, d_status);
+        if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, t->num_sms, s);
     }
     cudaFreeAsync(scratch, s);
     return st;
@@ -516,7 +564,7 @@ extern "C" htex_status htex_queries_sort(const htex_textures* t, const htex_quer
         cudaGetLastError();
         return HTEX_ERR_OUT_OF_MEMORY;
     }
-    const htex_status st = launch_sort(t, P, q, n, static_cast<uint32_t*>(counters), sorted, pos, 0, s);
+    const htex_status st = launch_sort<1>(t, P, words(q), n, static_cast<uint32_t*>(counters), words(sorted), pos, 0, s);
     cudaFreeAsync(counters, s);
     return st;
 }

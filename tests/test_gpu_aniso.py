@@ -129,3 +129,27 @@ def test_aniso_invalid_queries_and_arguments():
         with pytest.raises(hx.HtexError):
             hx.lookup_aniso(tl, q, bad)
     assert hx.lookup_aniso(tl, q[:0], 4).shape == (0, 2)
+
+
+def test_sorted_aniso_equals_unsorted_multi_chunk():
+    """HTEX_LOOKUP_BIN on the anisotropic lookup: 32-byte queries sorted by
+    halfedge range in chunks of 2^23 (a full chunk and a ragged one, invalid
+    queries inside) on a pool above the 64 MiB threshold give the unsorted
+    results bit for bit, and the oracle's on a sample."""
+    gen = lambda: syn.cylinder(around=128, rows=60, seed=14)
+    mo, to, tl = _case(gen, lambda E: np.full(E, 5, np.int32), 4, "u8", hx.BUILD_MIPS, seed=15)
+    assert tl.pool_bytes > (64 << 20)
+    n = (1 << 23) + 1237
+    qs = tuple(np.array(x) for x in _aniso_queries(mo.H, n, seed=16, lo=-8, hi=0))
+    qs[0][::70001] = -2
+    q = torch.from_numpy(hx.pack_queries_aniso(*qs)).cuda()
+    s0 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    a = hx.lookup_aniso(tl, q, 16, status=s0)
+    b = hx.lookup_aniso(tl, q, 16, status=s1, flags=hx.LOOKUP_BIN)
+    assert int(s0.item()) == int(s1.item()) == int((qs[0] < 0).sum())
+    assert torch.equal(torch.isnan(a), torch.isnan(b))
+    assert torch.equal(a.nan_to_num(nan=0.0), b.nan_to_num(nan=0.0))
+    sel = np.random.default_rng(17).choice(n, 20000, replace=False)
+    _cmp(b.cpu().numpy().astype(np.float64)[sel],
+         oracle.lookup_aniso(mo, to, tuple(x[sel] for x in qs), 16, nthreads=8), _tol(16, nmax=32))

@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "lookup_core.cuh"
+#include "aniso_launch.h"
 
 namespace htex {
 

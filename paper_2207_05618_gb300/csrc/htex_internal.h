@@ -104,14 +104,6 @@ htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int6
 htex_status htex_launch_backward(const htex_textures* t, const htex_query* q, int64_t n,
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);
-// Anisotropic lookups (aniso.cu), and the same on queries sorted by
-// halfedge range (HTEX_LOOKUP_BIN, lookup.cu), chunk by chunk, results
-// gathered back into query order.
-htex_status htex_launch_aniso(const htex_textures* t, const htex_query_aniso* q, int64_t n, int32_t kmax,
-                              float* out, htex_stream stream, int32_t* d_status);
-htex_status htex_launch_aniso_sorted(const htex_textures* t, const htex_query_aniso* q, int64_t n, int32_t kmax,
-                                     float* out, htex_stream stream, int32_t* d_status);
-
 // The adjoint on queries sorted by halfedge range (HTEX_LOOKUP_BIN), chunk
 // by chunk: the scatter-adds of neighbouring threads land in neighbouring
 // textures.  Falls back to the unsorted adjoint for pools that fit L2.

@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include "lookup_kernels.cuh"
+#include "aniso_launch.h"
 
 namespace htex {
 

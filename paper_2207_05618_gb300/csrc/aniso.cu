@@ -51,17 +51,46 @@ __device__ __forceinline__ TapsG taps_g(float p, int N) {
     return TapsG{i, (i >= 0 && i < N) ? 1.0f - a : 0.0f, (i + 1 >= 0 && i + 1 < N) ? a : 0.0f};
 }
 
+// Per-query constants of one fetch, fixed over its probes: where its two
+// levels start, their sizes and weights, how far outside the quad a probe
+// can still reach an in-bounds tap (half a texel of the coarsest level
+// read), the code factor and the Alg. 2 reflection.
+struct FetchConst {
+    int64_t base0, base1;   // byte offsets of texel (0, 0) of levels l0 and l1
+    int N0, N1;             // their sizes (l1 = l0 when one level is read)
+    float w0, w1;           // their weights (w1 = 0 when one level is read)
+    float half, sc;
+    bool flip, two;
+};
+
+template <int DT, int C>
+__device__ __forceinline__ FetchConst fetch_const(const TexRef& t, const Lod& d, uint32_t code) {
+    constexpr int TB = C * Fmt<DT>::ES;
+    FetchConst f;
+    const int l1 = d.l1 >= 0 ? d.l1 : d.l0;
+    f.N0 = 1 << (t.n - d.l0);
+    f.N1 = 1 << (t.n - l1);
+    f.base0 = int64_t(t.off) + int64_t(level_texels(t.n, d.l0)) * TB;
+    f.base1 = int64_t(t.off) + int64_t(level_texels(t.n, l1)) * TB;
+    f.two = d.l1 >= 0;
+    f.w0 = d.w0;
+    f.w1 = f.two ? d.w1 : 0.0f;
+    f.half = 0.5f / float(f.N1);
+    f.sc = code_factor<DT>(t);
+    f.flip = code & kFlipBit;
+    return f;
+}
+
 // One level of one fetch at quad coordinates (x, y) with level weight wl.
 template <int DT, int C>
-__device__ __forceinline__ void aniso_level(const Asset<GlobalSpace>& A, const TexRef& t, int l, float x, float y,
+__device__ __forceinline__ void aniso_level(const Asset<GlobalSpace>& A, int64_t base, int N, float x, float y,
                                             float wl, float sc, float (&acc)[C], float& W) {
     constexpr int TB = C * Fmt<DT>::ES;
-    const int N = 1 << (t.n - l);
     const TapsG tx = taps_g(x, N), ty = taps_g(y, N);
     W += wl * (tx.w0 + tx.w1) * (ty.w0 + ty.w1);
     const float y0 = ty.w0 * wl, y1 = ty.w1 * wl;
     const float w[4] = {y0 * tx.w0, y0 * tx.w1, y1 * tx.w0, y1 * tx.w1};
-    const int64_t o = int64_t(t.off) + int64_t(level_texels(t.n, l)) * TB + (int64_t(ty.i) * N + tx.i) * TB;
+    const int64_t o = base + (int64_t(ty.i) * N + tx.i) * TB;
     const int64_t d[4] = {0, TB, int64_t(N) * TB, int64_t(N) * TB + TB};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -76,18 +105,14 @@ __device__ __forceinline__ void aniso_level(const Asset<GlobalSpace>& A, const T
 // One fetch of one probe (one or two levels), skipped when no lane of the
 // warp has a tap in bounds.
 template <int DT, int C>
-__device__ __forceinline__ void aniso_fetch(const Asset<GlobalSpace>& A, unsigned act, bool ok, const TexRef& t,
-                                            const Lod& d, uint32_t code, float a, float b, float (&acc)[C],
-                                            float& W) {
-    const bool flip = code & kFlipBit;
-    const float x = flip ? 1.0f - a : a, y = flip ? 1.0f - b : b;
-    const float half = 0.5f / float(1 << (t.n - coarsest(d)));   // half a texel of the coarsest level read
-    const bool near = ok && x > -half && x < 1.0f + half && y > -half && y < 1.0f + half;
+__device__ __forceinline__ void aniso_fetch(const Asset<GlobalSpace>& A, unsigned act, bool ok, const FetchConst& f,
+                                            float a, float b, float (&acc)[C], float& W) {
+    const float x = f.flip ? 1.0f - a : a, y = f.flip ? 1.0f - b : b;
+    const bool near = ok && x > -f.half && x < 1.0f + f.half && y > -f.half && y < 1.0f + f.half;
     if (!__any_sync(act, near)) return;
-    const float sc = code_factor<DT>(t);
-    aniso_level<DT, C>(A, t, d.l0, x, y, near ? d.w0 : 0.0f, sc, acc, W);
-    if (__any_sync(act, near && d.l1 >= 0))
-        aniso_level<DT, C>(A, t, d.l1 >= 0 ? d.l1 : d.l0, x, y, (near && d.l1 >= 0) ? d.w1 : 0.0f, sc, acc, W);
+    aniso_level<DT, C>(A, f.base0, f.N0, x, y, near ? f.w0 : 0.0f, f.sc, acc, W);
+    if (__any_sync(act, near && f.two))
+        aniso_level<DT, C>(A, f.base1, f.N1, x, y, (near && f.two) ? f.w1 : 0.0f, f.sc, acc, W);
 }
 
 // Probe count (see the file comment): same float operations as the oracle.
@@ -130,7 +155,9 @@ __global__ void __launch_bounds__(256) k_lookup_aniso(Asset<GlobalSpace> A, Anis
         const TexRef to = tex_ref<DT>(A, rec.x & ~kFlipBit);
         const TexRef tn = tex_ref<DT>(A, rec.y & ~kFlipBit);
         const TexRef tp = tex_ref<DT>(A, rec.z & ~kFlipBit);
-        const Lod dn0 = select_lod(lf, to.n), dn1 = select_lod(lf, tn.n), dn2 = select_lod(lf, tp.n);
+        const FetchConst f0 = fetch_const<DT, C>(to, select_lod(lf, to.n), rec.x);
+        const FetchConst f1 = fetch_const<DT, C>(tn, select_lod(lf, tn.n), rec.y);
+        const FetchConst f2 = fetch_const<DT, C>(tp, select_lod(lf, tp.n), rec.z);
 
         float acc[C];
 #pragma unroll
@@ -142,9 +169,9 @@ __global__ void __launch_bounds__(256) k_lookup_aniso(Asset<GlobalSpace> A, Anis
             const bool on = ok && k < K;
             const float t = (float(2 * k + 1) - float(K)) / float(2 * K);
             const float pu = fmaf(mu, t, u), pv = fmaf(mv, t, v);
-            aniso_fetch<DT, C>(A, act, on, to, dn0, rec.x, pu, pv, acc, W);
-            aniso_fetch<DT, C>(A, act, on, tn, dn1, rec.y, pv, -pu, acc, W);
-            aniso_fetch<DT, C>(A, act, on, tp, dn2, rec.z, -pv, pu, acc, W);
+            aniso_fetch<DT, C>(A, act, on, f0, pu, pv, acc, W);
+            aniso_fetch<DT, C>(A, act, on, f1, pv, -pu, acc, W);
+            aniso_fetch<DT, C>(A, act, on, f2, -pv, pu, acc, W);
         }
         // invalid queries (W = 0, acc = 0): 0 * inf = NaN, as in the isotropic lookup
         const float inv = __frcp_rn(W);

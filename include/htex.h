@@ -352,13 +352,18 @@ htex_status htex_lookup_host(const htex_textures* t, const htex_query* q, int64_
  *                (the caller zeroes it); padding elements stay untouched
  *   flags        HTEX_LOOKUP_BIN: when the pool exceeds 64 MiB, sort the
  *                queries as htex_lookup does (chunks of 2^23, ranges of
- *                consecutive halfedges; grad_out rows follow their queries)
- *                so that neighbouring threads add into neighbouring
- *                textures; scratch of 20 + 4 * channels bytes per chunk
- *                query from the library pool.  HTEX_LOOKUP_GLOBAL ignored.
+ *                consecutive halfedges; grad_out rows move with their
+ *                queries) so that the threads resident together add into
+ *                a narrow range of textures; lanes of a warp whose taps
+ *                coincide (the same texture, level and 2x2 block or edge
+ *                texel pair) sum their contributions across the warp and
+ *                one lane issues the atomics.  Scratch of 16 + 4 * channels
+ *                bytes per chunk query from the library pool.
+ *                HTEX_LOOKUP_GLOBAL ignored.
  *   d_status     as for htex_lookup
- * Uses float atomics: the summation order, hence the last bits, may vary
- * from run to run.  Asynchronous. */
+ * Uses float atomics (a float2 and a scalar one per three-channel texel
+ * when grad_texels is 8-byte aligned): the summation order, hence the last
+ * bits, may vary from run to run.  Asynchronous. */
 htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, int64_t n,
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);
@@ -447,9 +452,12 @@ htex_status htex_displace(const htex_geometry* g, const htex_textures* t, int32_
  *     evicting the least recently used assets that no admitted request
  *     still needs; requests whose asset does not fit yet wait (later
  *     requests whose asset fits go ahead);
- *   - fills each free batch slot from the admitted requests in arrival
- *     order, at most request_chunk queries of one request per batch, so a
- *     request that arrives while others run joins the next batch;
+ *   - fills each free batch slot from the admitted requests, shortest
+ *     remaining work first with ageing (the remaining query count is
+ *     divided by 1 + wait / 1 ms, so small requests overtake large ones
+ *     and a waiting request keeps moving forward), at most request_chunk
+ *     queries of one request per batch, so a request that arrives while
+ *     others run joins the next batch;
  *   - launches a batch as an instantiated CUDA graph (descriptor table
  *     copy, then one persistent kernel per texel format pulling 4096-query
  *     tiles of any request), with the query and result copies around it.
@@ -520,17 +528,20 @@ void htex_server_destroy(htex_server* s);
  * load to make their own, and frame loops that cannot absorb the
  * device-wide synchronisation that cudaMalloc and cudaFree may cause.
  *
- * htex_lookup_noalloc computes exactly what htex_lookup with
- * HTEX_LOOKUP_BIN computes (same arguments, same results), without any
- * allocation: its scratch (the reordered queries, their original indices
- * and the bucket counters) is one fixed device array inside the library,
- * about 20 MiB, which every device that loads the library holds until the process
- * exits.
+ * htex_lookup_noalloc returns what htex_lookup with HTEX_LOOKUP_BIN
+ * returns for the same arguments, bit for bit (the same per-query filter
+ * code; only the order in which the queries are filtered differs), without
+ * any allocation: its scratch (the reordered queries, their original
+ * indices and the bucket counters) is one fixed device array inside the
+ * library, about 20 MiB, which every device that loads the library holds
+ * until the process exits.
  *   n         at most htex_lookup_noalloc_max_queries() (1,048,576);
  *             larger n returns HTEX_ERR_UNSUPPORTED before any device work
  * The first call made with a given device current looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call on every stream shares the one array and the
+ * device address (cudaGetSymbolAddress) and keeps it for the rest of the
+ * process; make that first call before any stream capture, and do not use
+ * this entry point again after cudaDeviceReset (the module, and with it
+ * the array, may then live at another address).  Every call on every stream shares the one array and the
  * array keeps the previous call's contents (the call clears its counters
  * itself), so calls whose device work overlaps (different streams without
  * ordering between them) race and must not be issued.  The textures must

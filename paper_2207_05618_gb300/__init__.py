@@ -347,28 +347,45 @@ def _autograd():
     import torch
 
     class HtexLookup(torch.autograd.Function):
-        """out = lookup(tex, queries) with d out / d texels through htex_lookup_backward.
+        """Differentiable lookups of an FP32 asset:
+        ``out = HtexLookup.apply(texels, tex, queries, flags)``.
 
-        ``texels`` is a pool-shaped float32 tensor that stands for the
-        resident pool (its values live in ``tex``); its gradient is the
-        pool-shaped texel gradient."""
+        ``texels``: contiguous float32 CUDA tensor of ``tex.pool_elements``
+        values, the stored texels in pool order (every texture at its pool
+        offset, levels consecutive, row-major [N][N][C]; padding elements are
+        ignored).  The forward pass writes them into the resident pool
+        (htex_textures_write_pool, a device-to-device copy on the current
+        stream) and runs htex_lookup, so the result is always the lookup of
+        exactly these values; the backward pass returns d loss / d texels in
+        the same layout (htex_lookup_backward).  ``flags``: HTEX_LOOKUP_BIN
+        sorts the queries in both passes.  The queries get no gradient."""
 
         @staticmethod
-        def forward(ctx, texels, tex, queries):
+        def forward(ctx, texels, tex, queries, flags=0):
+            if tex.dtype != "f32":
+                raise ValueError("HtexLookup needs an FP32 asset (its texels are the stored values)")
+            if not (isinstance(texels, torch.Tensor) and texels.is_cuda and texels.dtype == torch.float32
+                    and texels.is_contiguous() and texels.numel() == tex.pool_elements):
+                raise ValueError("texels must be a contiguous float32 CUDA tensor of tex.pool_elements values")
+            tex.write_pool(texels.detach())
             ctx.tex = tex
+            ctx.flags = int(flags)
             ctx.save_for_backward(queries)
-            return lookup(tex, queries)
+            return lookup(tex, queries, flags=flags)
 
         @staticmethod
         def backward(ctx, grad_out):
             (queries,) = ctx.saved_tensors
-            g = lookup_backward(ctx.tex, queries, grad_out.contiguous().float())
-            return g, None, None
+            g = None
+            if ctx.needs_input_grad[0]:
+                g = lookup_backward(ctx.tex, queries, grad_out.contiguous().float(), flags=ctx.flags)
+            return g, None, None, None
 
     return HtexLookup
 
 
 class _LazyFn:
+    """HtexLookup, created on first use (torch is imported lazily)."""
     _fn = None
 
     def apply(self, *a):

@@ -6,7 +6,25 @@
 // query the kernel first recomputes W from the coordinates alone (no texel
 // loads), then scatter-adds grad_out * w_k / W into every in-bounds tap
 // with nonzero weight: float4/float2 atomics where a texel's channels are
-// contiguous and aligned, scalar atomics otherwise.
+// contiguous and aligned (three-channel texels: one float2 and one scalar
+// atomic), scalar atomics otherwise.
+//
+// Every lane of a warp runs every iteration of the grid-stride loop (lanes
+// past the end carry no query), so warp-wide collectives always see all 32
+// lanes; the query two iterations ahead and the record and upstream
+// gradient one iteration ahead are in flight while the current query is
+// scattered.
+//
+// Warp-aggregated variant (AGG, used after the queries are sorted by
+// halfedge range, HTEX_LOOKUP_BIN): a query's taps come in parts -- the own fetch's 2x2
+// block at each of its levels, and the two-texel row or column of the
+// Next and Prev fetches at each level.  A part's taps are fixed by (texture,
+// level, first tap index, side), so lanes whose parts have equal keys
+// (__match_any_sync) add into the same texels: their values are summed
+// across the group with shuffles and only the group's lowest lane issues
+// the atomics.  Lanes on the same coarse level of one texture collapse to
+// one atomic per texel; a warp with no shared part pays one match and one
+// vote per part.
 #include <algorithm>
 #include <cmath>
 
@@ -16,12 +34,15 @@
 
 namespace htex {
 
+constexpr unsigned kFull = 0xffffffffu;
+
 struct BwdParams {
     const htex_query* q;
     int64_t n;
     const float* gout;
     float* grad;
     int32_t* status;
+    bool pair_ok;   // grad is 8-byte aligned: three-channel texels take a float2 atomic
 };
 
 // The forward weights, recomputed: each fetch decomposed as in the forward
@@ -40,46 +61,133 @@ __device__ __forceinline__ float edge_weight(int n, int l, float dist, float alo
     return wa * (ta.w0 + ta.w1);
 }
 
+// One texel's C values added into the gradient at element index elem.
 template <int C>
-__device__ __forceinline__ void add_texel(float* grad, uint64_t elem, float w, const float (&g)[C]) {
-    if (w == 0.0f) return;
+__device__ __forceinline__ void red_texel(float* grad, uint64_t elem, const float* x, bool pair_ok) {
     if constexpr (C == 4) {
-        atomicAdd(reinterpret_cast<float4*>(grad + elem), make_float4(w * g[0], w * g[1], w * g[2], w * g[3]));
+        atomicAdd(reinterpret_cast<float4*>(grad + elem), make_float4(x[0], x[1], x[2], x[3]));
     } else if constexpr (C == 2) {
-        atomicAdd(reinterpret_cast<float2*>(grad + elem), make_float2(w * g[0], w * g[1]));
-    } else {
+        atomicAdd(reinterpret_cast<float2*>(grad + elem), make_float2(x[0], x[1]));
+    } else if constexpr (C == 3) {
+        if (pair_ok) {   // the 8-byte-aligned pair of the three channels, then the third alone
+            const bool even = (elem & 1u) == 0;
+            atomicAdd(reinterpret_cast<float2*>(grad + elem + (even ? 0 : 1)),
+                      even ? make_float2(x[0], x[1]) : make_float2(x[1], x[2]));
+            atomicAdd(grad + elem + (even ? 2 : 0), even ? x[2] : x[0]);
+        } else {
 #pragma unroll
-        for (int c = 0; c < C; ++c) atomicAdd(grad + elem + c, w * g[c]);
+            for (int c = 0; c < 3; ++c) atomicAdd(grad + elem + c, x[c]);
+        }
+    } else {
+        atomicAdd(grad + elem, x[0]);
     }
 }
 
-template <int DT, int C>
-__device__ __forceinline__ void own_scatter(float* grad, const TexRef& t, int l, float x, float y, float wl,
-                                            const float (&g)[C]) {
-    constexpr int ES = Fmt<DT>::ES;
-    const int N = 1 << (t.n - l);
-    const Taps1 tx = taps1(x, N), ty = taps1(y, N);
-    const uint64_t lvl = t.off / ES + uint64_t(level_texels(t.n, l)) * C;   // element index
-    add_texel<C>(grad, lvl + uint64_t(ty.i0 * N + tx.i0) * C, wl * ty.w0 * tx.w0, g);
-    add_texel<C>(grad, lvl + uint64_t(ty.i0 * N + tx.i1) * C, wl * ty.w0 * tx.w1, g);
-    add_texel<C>(grad, lvl + uint64_t(ty.i1 * N + tx.i0) * C, wl * ty.w1 * tx.w0, g);
-    add_texel<C>(grad, lvl + uint64_t(ty.i1 * N + tx.i1) * C, wl * ty.w1 * tx.w1, g);
+// Sum of x over the lanes of the calling lane's group (peers: the lanes with
+// an equal key, from __match_any_sync); the group's lowest lane ends up
+// holding the total.  All 32 lanes call it together.  A tree over group
+// ranks: at step s, the lane of rank r adds the partial sum of rank r + s.
+template <int K>
+__device__ __forceinline__ void group_sum(unsigned peers, float (&x)[K]) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned most = __reduce_max_sync(kFull, unsigned(__popc(peers)));
+    unsigned above = peers & ~((2u << lane) - 1u);   // group members above this lane
+    int dropped = 0;
+    for (unsigned s = 1; s < most; s <<= 1) {
+        while (dropped < int(s) - 1) {   // keep the members from rank + s up
+            above &= above - 1u;
+            ++dropped;
+        }
+        const bool has = above != 0u;
+        const int src = has ? __ffs(above) - 1 : int(lane);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float o = __shfl_sync(kFull, x[k], src);
+            if (has) x[k] += o;
+        }
+    }
 }
 
-template <int DT, int C, bool ROW>
-__device__ __forceinline__ void edge_scatter(float* grad, const TexRef& t, int l, float dist, float along, bool flip,
-                                             float wl, const float (&g)[C]) {
-    constexpr int ES = Fmt<DT>::ES;
+__device__ __forceinline__ bool lowest_of(unsigned peers) {
+    return (peers & ((1u << (threadIdx.x & 31u)) - 1u)) == 0u;
+}
+
+// The own fetch's 2x2 block at level l: taps (i, j), (i + 1, j), (i, j + 1),
+// (i + 1, j + 1) of weight wl * w_x * w_y, into element index
+// level start + (row * N + column) * C.
+template <int DT, int C, bool AGG>
+__device__ __forceinline__ void own_part(const BwdParams& p, const TexRef& t, uint32_t e, int l, float x, float y,
+                                         float wl, bool on, const float (&g)[C]) {
+    const int N = 1 << (t.n - l);
+    const TapsU tx = taps_u(x, N), ty = taps_u(y, N);
+    const float w[4] = {wl * ty.w0 * tx.w0, wl * ty.w0 * tx.w1, wl * ty.w1 * tx.w0, wl * ty.w1 * tx.w1};
+    const bool inb[4] = {tx.i >= 0 && ty.i >= 0, tx.i + 1 < N && ty.i >= 0, tx.i >= 0 && ty.i + 1 < N,
+                         tx.i + 1 < N && ty.i + 1 < N};
+    float v[4 * C];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[k * C + c] = w[k] * g[c];
+    bool summed = false;
+    if constexpr (AGG) {
+        const unsigned long long key =
+            on ? (uint64_t(e) << 32) | (uint32_t(l) << 28) | (uint32_t(ty.i + 1) << 14) | uint32_t(tx.i + 1)
+               : ~0ull;
+        const unsigned peers = __match_any_sync(kFull, key);
+        if (__any_sync(kFull, on && peers != (1u << (threadIdx.x & 31u)))) {
+            group_sum<4 * C>(peers, v);
+            summed = true;
+            on = on && lowest_of(peers);
+        }
+    }
+    if (!on) return;
+    const int64_t b = int64_t(t.off / Fmt<DT>::ES + uint64_t(level_texels(t.n, l)) * C) +
+                      (int64_t(ty.i) * N + tx.i) * C;
+    const int64_t o[4] = {0, C, int64_t(N) * C, int64_t(N + 1) * C};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (inb[k] && (summed || w[k] != 0.0f)) red_texel<C>(p.grad, uint64_t(b + o[k]), v + k * C, p.pair_ok);
+}
+
+// A Next (row) or Prev (column) fetch at level l: the two texels of row or
+// column k (0, or N - 1 when Alg. 2 reflects the quad) on the shared side,
+// at positions i and i + 1 along it.
+template <int DT, int C, bool AGG>
+__device__ __forceinline__ void edge_part(const BwdParams& p, const TexRef& t, uint32_t e, int l, float dist,
+                                          float along, bool flip, bool row, float wl, bool on,
+                                          const float (&g)[C]) {
     const int N = 1 << (t.n - l);
     const float wa = across_weight(dist, N);
-    if (!(wa > 0.0f)) return;
-    const Taps1 ta = taps1(flip ? 1.0f - along : along, N);
+    on = on && wa > 0.0f;
+    const TapsU ta = taps_u(flip ? 1.0f - along : along, N);
+    const float w[2] = {wl * wa * ta.w0, wl * wa * ta.w1};
+    const bool inb[2] = {ta.i >= 0, ta.i + 1 < N};
+    float v[2 * C];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int c = 0; c < C; ++c) v[k * C + c] = w[k] * g[c];
+    bool summed = false;
+    if constexpr (AGG) {
+        const unsigned long long key =
+            on ? (uint64_t(e) << 32) | (uint32_t(l) << 28) | (uint32_t(row) << 27) | (uint32_t(flip) << 26) |
+                     uint32_t(ta.i + 1)
+               : ~0ull;
+        const unsigned peers = __match_any_sync(kFull, key);
+        if (__any_sync(kFull, on && peers != (1u << (threadIdx.x & 31u)))) {
+            group_sum<2 * C>(peers, v);
+            summed = true;
+            on = on && lowest_of(peers);
+        }
+    }
+    if (!on) return;
     const int k = flip ? N - 1 : 0;
-    const uint64_t lvl = t.off / ES + uint64_t(level_texels(t.n, l)) * C;
-    const uint64_t e0 = ROW ? uint64_t(k * N + ta.i0) : uint64_t(ta.i0 * N + k);
-    const uint64_t e1 = ROW ? uint64_t(k * N + ta.i1) : uint64_t(ta.i1 * N + k);
-    add_texel<C>(grad, lvl + e0 * C, wl * wa * ta.w0, g);
-    add_texel<C>(grad, lvl + e1 * C, wl * wa * ta.w1, g);
+    const int64_t step = row ? 1 : N;
+    const int64_t b = int64_t(t.off / Fmt<DT>::ES + uint64_t(level_texels(t.n, l)) * C) +
+                      ((row ? int64_t(k) * N : int64_t(k)) + int64_t(ta.i) * step) * C;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+        if (inb[q] && (summed || w[q] != 0.0f)) red_texel<C>(p.grad, uint64_t(b + q * step * C), v + q * C, p.pair_ok);
 }
 
 // One query's three fetches: their textures, level choices and coordinates.
@@ -87,6 +195,7 @@ struct Fetches {
     TexRef t[3];
     Lod d[3];
     bool flip[3];
+    uint32_t e[3];
 };
 
 template <int DT, class S>
@@ -95,43 +204,100 @@ __device__ __forceinline__ Fetches plan(const Asset<S>& A, uint4 rec, float lf) 
     const uint32_t code[3] = {rec.x, rec.y, rec.z};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        F.t[k] = tex_ref<DT>(A, code[k] & ~kFlipBit);
+        F.e[k] = code[k] & ~kFlipBit;
+        F.t[k] = tex_ref<DT>(A, F.e[k]);
         F.d[k] = select_lod(lf, F.t[k].n);
         F.flip[k] = code[k] & kFlipBit;
     }
     return F;
 }
 
-template <int DT, int C>
-__global__ void __launch_bounds__(256) k_backward(Asset<GlobalSpace> A, BwdParams p) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        int h;
-        float u, v, f;
-        if (!decode_query(ld_query(p.q, i), A.H, h, u, v, f)) {
-            if (p.status) atomicAdd(p.status, 1);
-            continue;
-        }
-        const uint4 rec = A.rec.ld16(uint64_t(h) * 16u);
-        const Fetches F = plan<DT>(A, rec, footprint_log2(f));
-        const float x = F.flip[0] ? 1.0f - u : u, y = F.flip[0] ? 1.0f - v : v;
-        float W = 0.0f;
-        W = fmaf(F.d[0].w0, own_weight(F.t[0].n, F.d[0].l0, x, y), W);
-        if (F.d[0].l1 >= 0) W = fmaf(F.d[0].w1, own_weight(F.t[0].n, F.d[0].l1, x, y), W);
-        W = fmaf(F.d[1].w0, edge_weight(F.t[1].n, F.d[1].l0, u, v, F.flip[1]), W);
-        if (F.d[1].l1 >= 0) W = fmaf(F.d[1].w1, edge_weight(F.t[1].n, F.d[1].l1, u, v, F.flip[1]), W);
-        W = fmaf(F.d[2].w0, edge_weight(F.t[2].n, F.d[2].l0, v, u, F.flip[2]), W);
-        if (F.d[2].l1 >= 0) W = fmaf(F.d[2].w1, edge_weight(F.t[2].n, F.d[2].l1, v, u, F.flip[2]), W);
-        const float inv = __frcp_rn(W);
-        float g[C];
+template <int C>
+__device__ __forceinline__ void load_gout(const BwdParams& p, int64_t i, bool valid, float (&g)[C]) {
+    if constexpr (C == 4) {
+        const float4 r = valid ? __ldcs(reinterpret_cast<const float4*>(p.gout) + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        g[0] = r.x; g[1] = r.y; g[2] = r.z; g[3] = r.w;
+    } else {
 #pragma unroll
-        for (int c = 0; c < C; ++c) g[c] = __ldcs(p.gout + i * C + c) * inv;
-        own_scatter<DT, C>(p.grad, F.t[0], F.d[0].l0, x, y, F.d[0].w0, g);
-        if (F.d[0].l1 >= 0) own_scatter<DT, C>(p.grad, F.t[0], F.d[0].l1, x, y, F.d[0].w1, g);
-        edge_scatter<DT, C, true>(p.grad, F.t[1], F.d[1].l0, u, v, F.flip[1], F.d[1].w0, g);
-        if (F.d[1].l1 >= 0) edge_scatter<DT, C, true>(p.grad, F.t[1], F.d[1].l1, u, v, F.flip[1], F.d[1].w1, g);
-        edge_scatter<DT, C, false>(p.grad, F.t[2], F.d[2].l0, v, u, F.flip[2], F.d[2].w0, g);
-        if (F.d[2].l1 >= 0) edge_scatter<DT, C, false>(p.grad, F.t[2], F.d[2].l1, v, u, F.flip[2], F.d[2].w1, g);
+        for (int c = 0; c < C; ++c) g[c] = valid ? __ldcs(p.gout + i * C + c) : 0.0f;
+    }
+}
+
+// The adjoint of one query (valid: the lane holds a query of the batch).
+template <int DT, int C, bool AGG>
+__device__ __forceinline__ void scatter_one(const Asset<GlobalSpace>& A, const BwdParams& p, bool valid, int4 raw,
+                                            uint4 rec, const float (&gin)[C]) {
+    int h;
+    float u, v, f;
+    bool ok = valid && decode_query(raw, A.H, h, u, v, f);
+    if (valid && !ok && p.status) atomicAdd(p.status, 1);
+    if (!ok) {
+        u = 0.0f;
+        v = 0.0f;
+        f = 0.0f;
+        rec = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const Fetches F = plan<DT>(A, rec, footprint_log2(f));
+    const float x = F.flip[0] ? 1.0f - u : u, y = F.flip[0] ? 1.0f - v : v;
+    float W = 0.0f;
+    W = fmaf(F.d[0].w0, own_weight(F.t[0].n, F.d[0].l0, x, y), W);
+    if (F.d[0].l1 >= 0) W = fmaf(F.d[0].w1, own_weight(F.t[0].n, F.d[0].l1, x, y), W);
+    W = fmaf(F.d[1].w0, edge_weight(F.t[1].n, F.d[1].l0, u, v, F.flip[1]), W);
+    if (F.d[1].l1 >= 0) W = fmaf(F.d[1].w1, edge_weight(F.t[1].n, F.d[1].l1, u, v, F.flip[1]), W);
+    W = fmaf(F.d[2].w0, edge_weight(F.t[2].n, F.d[2].l0, v, u, F.flip[2]), W);
+    if (F.d[2].l1 >= 0) W = fmaf(F.d[2].w1, edge_weight(F.t[2].n, F.d[2].l1, v, u, F.flip[2]), W);
+    const float inv = ok ? __frcp_rn(W) : 0.0f;
+    float g[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) g[c] = gin[c] * inv;
+
+    // own fetch (one or two levels), then Next (row, distance u, along v) and
+    // Prev (column, distance v, along u); parts no lane needs are skipped
+    own_part<DT, C, AGG>(p, F.t[0], F.e[0], F.d[0].l0, x, y, F.d[0].w0, ok, g);
+    const bool own2 = ok && F.d[0].l1 >= 0;
+    if (__any_sync(kFull, own2))
+        own_part<DT, C, AGG>(p, F.t[0], F.e[0], own2 ? F.d[0].l1 : F.d[0].l0, x, y, F.d[0].w1, own2, g);
+#pragma unroll
+    for (int k = 1; k < 3; ++k) {
+        const bool row = k == 1;
+        const float dist = row ? u : v, along = row ? v : u;
+        const int cl = F.d[k].l1 >= 0 ? F.d[k].l1 : F.d[k].l0;   // coarsest level: the widest reach
+        const bool near = ok && across_weight(dist, 1 << (F.t[k].n - cl)) > 0.0f;
+        if (!__any_sync(kFull, near)) continue;
+        edge_part<DT, C, AGG>(p, F.t[k], F.e[k], F.d[k].l0, dist, along, F.flip[k], row, F.d[k].w0, near, g);
+        const bool two = near && F.d[k].l1 >= 0;
+        if (__any_sync(kFull, two))
+            edge_part<DT, C, AGG>(p, F.t[k], F.e[k], two ? F.d[k].l1 : F.d[k].l0, dist, along, F.flip[k], row,
+                                  F.d[k].w1, two, g);
+    }
+}
+
+template <int DT, int C, bool AGG>
+__global__ void __launch_bounds__(256, 3) k_backward(Asset<GlobalSpace> A, BwdParams p) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    int64_t base = i - int64_t(threadIdx.x & 31u);   // the warp's first query: the loop is warp-uniform
+    if (base >= p.n) return;
+    const int4 none = make_int4(-1, 0, 0, 0);
+    int4 raw0 = i < p.n ? ld_query(p.q, i) : none;
+    int4 raw1 = i + stride < p.n ? ld_query(p.q, i + stride) : none;
+    uint4 rec0 = i < p.n ? A.rec.ld16(uint64_t(unsigned(raw0.x) < unsigned(A.H) ? raw0.x : 0) * 16u)
+                         : make_uint4(0u, 0u, 0u, 0u);
+    float g0[C];
+    load_gout<C>(p, i, i < p.n, g0);
+    for (; base < p.n; base += stride, i += stride) {
+        const int64_t i1 = i + stride, i2 = i + 2 * stride;
+        const int4 raw2 = i2 < p.n ? ld_query(p.q, i2) : none;
+        const uint4 rec1 = i1 < p.n ? A.rec.ld16(uint64_t(unsigned(raw1.x) < unsigned(A.H) ? raw1.x : 0) * 16u)
+                                    : make_uint4(0u, 0u, 0u, 0u);
+        float g1[C];
+        load_gout<C>(p, i1, i1 < p.n, g1);
+        scatter_one<DT, C, AGG>(A, p, i < p.n, raw0, rec0, g0);
+        raw0 = raw1;
+        raw1 = raw2;
+        rec0 = rec1;
+#pragma unroll
+        for (int c = 0; c < C; ++c) g0[c] = g1[c];
     }
 }
 
@@ -143,17 +309,10 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <int DT, int C>
+template <int DT, int C, bool AGG>
 htex_status launch_bwd(const htex_textures* t, const BwdParams& p, cudaStream_t s) {
-    Asset<GlobalSpace> A;
-    A.rec.base = static_cast<const uint8_t*>(t->d_rec);
-    A.hdr.base = static_cast<const uint8_t*>(t->d_hdr);
-    A.scale.base = static_cast<const uint8_t*>(t->d_scale);
-    A.pool.base = static_cast<const uint8_t*>(t->d_pool);
-    A.H = t->H;
-    A.uniform_log2n = t->uniform_log2n;
-    A.uniform_stride16 = uint32_t(t->uniform_stride / 16);
-    auto k = k_backward<DT, C>;
+    const Asset<GlobalSpace> A = global_asset(t);
+    auto k = k_backward<DT, C, AGG>;
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kThreads, 0) != cudaSuccess || b < 1) b = 1;
     const int64_t want = (p.n + kThreads - 1) / kThreads;
@@ -162,13 +321,25 @@ htex_status launch_bwd(const htex_textures* t, const BwdParams& p, cudaStream_t 
     return cudaGetLastError() == cudaSuccess ? HTEX_OK : HTEX_ERR_CUDA;
 }
 
-template <int DT>
+template <int DT, bool AGG>
 htex_status launch_bwd_c(const htex_textures* t, const BwdParams& p, cudaStream_t s) {
     switch (t->C) {
-    case 1: return launch_bwd<DT, 1>(t, p, s);
-    case 2: return launch_bwd<DT, 2>(t, p, s);
-    case 3: return launch_bwd<DT, 3>(t, p, s);
-    case 4: return launch_bwd<DT, 4>(t, p, s);
+    case 1: return launch_bwd<DT, 1, AGG>(t, p, s);
+    case 2: return launch_bwd<DT, 2, AGG>(t, p, s);
+    case 3: return launch_bwd<DT, 3, AGG>(t, p, s);
+    case 4: return launch_bwd<DT, 4, AGG>(t, p, s);
+    }
+    return HTEX_ERR_INVALID_ARG;
+}
+
+template <bool AGG>
+htex_status launch_bwd_dt(const htex_textures* t, const BwdParams& p, cudaStream_t s) {
+    switch (t->dtype) {
+    case HTEX_F32: return launch_bwd_c<HTEX_F32, AGG>(t, p, s);
+    case HTEX_U8: return launch_bwd_c<HTEX_U8, AGG>(t, p, s);
+    case HTEX_F16: return launch_bwd_c<HTEX_F16, AGG>(t, p, s);
+    case HTEX_BF16: return launch_bwd_c<HTEX_BF16, AGG>(t, p, s);
+    case HTEX_E4M3: return launch_bwd_c<HTEX_E4M3, AGG>(t, p, s);
     }
     return HTEX_ERR_INVALID_ARG;
 }
@@ -177,17 +348,10 @@ htex_status launch_bwd_c(const htex_textures* t, const BwdParams& p, cudaStream_
 
 htex_status htex_launch_backward(const htex_textures* t, const htex_query* q, int64_t n, const float* grad_out,
                                  float* grad_texels, uint32_t flags, htex_stream stream, int32_t* d_status) {
-    (void)flags;
-    const BwdParams p{q, n, grad_out, grad_texels, d_status};
+    const BwdParams p{q, n, grad_out, grad_texels, d_status, (reinterpret_cast<uintptr_t>(grad_texels) & 7u) == 0};
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    switch (t->dtype) {
-    case HTEX_F32: return launch_bwd_c<HTEX_F32>(t, p, s);
-    case HTEX_U8: return launch_bwd_c<HTEX_U8>(t, p, s);
-    case HTEX_F16: return launch_bwd_c<HTEX_F16>(t, p, s);
-    case HTEX_BF16: return launch_bwd_c<HTEX_BF16>(t, p, s);
-    case HTEX_E4M3: return launch_bwd_c<HTEX_E4M3>(t, p, s);
-    }
-    return HTEX_ERR_INVALID_ARG;
+    if (flags & kBackwardAggregate) return launch_bwd_dt<true>(t, p, s);
+    return launch_bwd_dt<false>(t, p, s);
 }
 
 // ------------------------------------------------------ Adam on the pool

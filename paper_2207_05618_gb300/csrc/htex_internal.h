@@ -96,17 +96,28 @@ inline int64_t htex_level_texels(int n, int l) {
 int64_t htex_pool_offsets(int32_t E, const int32_t* log2n, int32_t C, htex_dtype dt,
                           int64_t* offsets /* [E+1], nullable */);
 
+// Stream-ordered scratch memory of the library: one pool per device that
+// keeps its memory between calls (lookup.cu).
+cudaMemPool_t htex_scratch_pool(int device);
+
+// log2 of the halfedges per sort range so that a range's textures take
+// about 32 MB; -1 when the pool is too small for sorting to pay (lookup.cu).
+int htex_bin_shift(const htex_textures* t);
+
 // Kernel launchers (lookup.cu, backward.cu).  They validate nothing: the
 // C-ABI entry points have checked every argument.
 htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int64_t n,
                                float* out, uint32_t flags, htex_stream stream,
                                int32_t* d_status);
+// flags: kBackwardAggregate merges the scatter-adds of lanes of a warp that
+// hit the same texels (for sorted queries); other bits are ignored.
+constexpr uint32_t kBackwardAggregate = 1u << 16;
 htex_status htex_launch_backward(const htex_textures* t, const htex_query* q, int64_t n,
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);
 // The adjoint on queries sorted by halfedge range (HTEX_LOOKUP_BIN), chunk
-// by chunk: the scatter-adds of neighbouring threads land in neighbouring
-// textures.  Falls back to the unsorted adjoint for pools that fit L2.
+// by chunk, with warp-aggregated atomics (lookup.cu).  Falls back to the
+// unsorted adjoint for pools that fit L2.
 htex_status htex_launch_backward_sorted(const htex_textures* t, const htex_query* q, int64_t n,
                                         const float* grad_out, float* grad_texels, htex_stream stream,
                                         int32_t* d_status);

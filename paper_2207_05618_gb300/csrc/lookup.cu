@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const htex_query* q
 constexpr int kSortThreads = 256;
 constexpr int kSortPer = 8;
 constexpr int kSortTile = kSortThreads * kSortPer;
-constexpr int kSortMaxBuckets = 512 + 2;   // keeps the scatter's static shared memory under 48 KiB
+constexpr int kSortMaxBuckets = 256;   // keeps the scatter's static shared memory under 48 KiB
 
 // QW: 16-byte words per query (1: htex_query, 2: htex_query_aniso); the
 // halfedge id is the first word's first int.
@@ -192,12 +192,16 @@ __device__ __forceinline__ void block_scan_buckets(const uint32_t* x, uint32_t* 
     __syncthreads();
 }
 
-template <int QW>
+// PC: floats of payload per query (rows of 'pay' in query order, moved to
+// 'spay' in sorted order with their queries); pos nullable.
+template <int QW, int PC>
 __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const int4* q, int64_t m, int32_t H, int shift,
                                                                 uint32_t B, const uint32_t* counts, uint32_t* taken,
-                                                                int4* sq, int32_t* pos, int32_t pos_base) {
-    constexpr int PER = kSortPer / QW, TILE = kSortThreads * PER;
+                                                                int4* sq, int32_t* pos, int32_t pos_base,
+                                                                const float* pay, float* spay) {
+    constexpr int PER = kSortPer / QW / (PC > 0 ? 2 : 1), TILE = kSortThreads * PER;
     __shared__ int4 tile[TILE * QW];
+    __shared__ float tile_pay[PC > 0 ? TILE * PC : 1];
     __shared__ uint16_t tile_bucket[TILE];
     __shared__ uint32_t start[kSortMaxBuckets];    // first sorted position of each bucket
     __shared__ uint32_t cnt[kSortMaxBuckets];      // the tile's bucket sizes
@@ -213,6 +217,7 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const int4* q, i
         for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = 0;
         __syncthreads();
         int4 r[PER][QW];
+        float pv[PER][PC > 0 ? PC : 1];
         uint32_t bk[PER], rank[PER];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
@@ -220,6 +225,9 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const int4* q, i
 #pragma unroll
             for (int w = 0; w < QW; ++w)
                 if (j < tm) r[k][w] = __ldcs(q + (t0 + j) * QW + w);
+#pragma unroll
+            for (int c = 0; c < PC; ++c)
+                if (j < tm) pv[k][c] = __ldcs(pay + (t0 + j) * PC + c);
         }
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
@@ -240,8 +248,10 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const int4* q, i
                 const uint32_t lp = loff[bk[k]] + rank[k];
 #pragma unroll
                 for (int w = 0; w < QW; ++w) tile[lp * QW + w] = r[k][w];
+#pragma unroll
+                for (int c = 0; c < PC; ++c) tile_pay[lp * PC + c] = pv[k][c];
                 tile_bucket[lp] = uint16_t(bk[k]);
-                __stcs(pos + t0 + j, pos_base + int32_t(gbase[bk[k]] + rank[k]));
+                if (pos) __stcs(pos + t0 + j, pos_base + int32_t(gbase[bk[k]] + rank[k]));
             }
         }
         __syncthreads();
@@ -250,25 +260,14 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const int4* q, i
             const uint32_t b = tile_bucket[j];
             sq[int64_t(gbase[b] + (uint32_t(j) - loff[b])) * QW + w] = tile[x];
         }
-        __syncthreads();
-    }
-}
-
-// Rows of a per-query array into sorted order: rows[pos[i]] = src[i] (the
-// adjoint's upstream gradients follow their queries).
-template <int C>
-__global__ void k_chunk_permute(const float* src, const int32_t* pos, int64_t m, float* rows) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < m; i += stride) {
-        const int64_t p = __ldcs(pos + i);
-        if constexpr (C == 4) {
-            reinterpret_cast<float4*>(rows)[p] = __ldcs(reinterpret_cast<const float4*>(src) + i);
-        } else if constexpr (C == 2) {
-            reinterpret_cast<float2*>(rows)[p] = __ldcs(reinterpret_cast<const float2*>(src) + i);
-        } else {
-#pragma unroll
-            for (int c = 0; c < C; ++c) rows[p * C + c] = __ldcs(src + i * C + c);
+        if constexpr (PC > 0) {
+            for (int x = threadIdx.x; x < tm * PC; x += kSortThreads) {
+                const int j = x / PC, c = x - j * PC;
+                const uint32_t b = tile_bucket[j];
+                spay[int64_t(gbase[b] + (uint32_t(j) - loff[b])) * PC + c] = tile_pay[x];
+            }
         }
+        __syncthreads();
     }
 }
 
@@ -331,9 +330,9 @@ htex_status launch_fwd_dt(const htex_textures* t, const FwdParams& p, uint32_t f
     return HTEX_ERR_INVALID_ARG;
 }
 
-// Stream-ordered scratch from a library-owned pool per device that keeps
-// its memory between calls.
-cudaMemPool_t scratch_pool(int device) {
+}  // namespace
+
+cudaMemPool_t htex_scratch_pool(int device) {
     static std::mutex mu;
     static cudaMemPool_t pools[64] = {};
     std::lock_guard<std::mutex> g(mu);
@@ -351,6 +350,8 @@ cudaMemPool_t scratch_pool(int device) {
     }
     return pools[device];
 }
+
+namespace {
 
 }  // namespace
 
@@ -384,21 +385,22 @@ SortPlan sort_plan(int32_t H) {
 size_t counter_bytes(const SortPlan& P) { return (size_t(2 * P.B) * 4 + 255) & ~size_t(255); }
 
 // Sorts q[0..m) into sq within consecutive chunks of kSortChunk queries;
-// pos[i] = pos_base + where query i went.  counters: counter_bytes(P) of
+// pos[i] = where query i went (nullable); PC floats of payload per query
+// follow their queries from pay to spay.  counters: counter_bytes(P) of
 // scratch.  QW: 16-byte words per query.
-template <int QW>
+template <int QW, int PC = 0>
 htex_status launch_sort(const htex_textures* t, const SortPlan& P, const int4* q, int64_t m, uint32_t* counters,
-                        int4* sq, int32_t* pos, int32_t pos_base, cudaStream_t s) {
-    constexpr int64_t TILE = int64_t(kSortThreads) * (kSortPer / QW);
-    const int64_t blocks = int64_t(t->num_sms) * resident_blocks(k_chunk_scatter<QW>, kSortThreads, 0);
+                        int4* sq, int32_t* pos, cudaStream_t s, const float* pay = nullptr, float* spay = nullptr) {
+    constexpr int64_t TILE = int64_t(kSortThreads) * (kSortPer / QW / (PC > 0 ? 2 : 1));
+    const int64_t blocks = int64_t(t->num_sms) * resident_blocks(k_chunk_scatter<QW, PC>, kSortThreads, 0);
     for (int64_t c0 = 0; c0 < m; c0 += kSortChunk) {
         const int64_t mc = std::min<int64_t>(kSortChunk, m - c0);
         const int64_t g = std::min<int64_t>((mc + TILE - 1) / TILE, blocks);
         if (cudaMemsetAsync(counters, 0, size_t(2 * P.B) * 4, s) != cudaSuccess) return HTEX_ERR_CUDA;
         k_chunk_count<QW><<<unsigned(g), kSortThreads, 0, s>>>(q + c0 * QW, mc, t->H, P.shift, P.B, counters);
-        k_chunk_scatter<QW><<<unsigned(g), kSortThreads, 0, s>>>(q + c0 * QW, mc, t->H, P.shift, P.B, counters,
-                                                                 counters + P.B, sq + c0 * QW, pos + c0,
-                                                                 pos_base + int32_t(c0));
+        k_chunk_scatter<QW, PC><<<unsigned(g), kSortThreads, 0, s>>>(
+            q + c0 * QW, mc, t->H, P.shift, P.B, counters, counters + P.B, sq + c0 * QW, pos ? pos + c0 : nullptr,
+            int32_t(c0), PC ? pay + c0 * PC : nullptr, PC ? spay + c0 * PC : nullptr);
         if (cudaGetLastError() != cudaSuccess) return HTEX_ERR_CUDA;
     }
     return HTEX_OK;
@@ -441,12 +443,15 @@ htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int6
         return launch_fwd_dt<false>(t, FwdParams{q, n, out, d_status, nullptr}, flags, s);
 
     // one chunk at a time: sort, filter into the sorted copy, gather back
+    // (storing each result straight to its query's row from the filter
+    // instead was measured slower: scattered 16-byte stores leave partly
+    // written sectors that DRAM has to merge)
     const SortPlan P = sort_plan(t->H);
     const int64_t M = std::min<int64_t>(n, kSortChunk);
     const size_t cnt_b = counter_bytes(P);
     const size_t sq_b = size_t(M) * 16, pos_b = (size_t(M) * 4 + 255) & ~size_t(255);
     const size_t sout_b = size_t(M) * 4 * size_t(t->C);
-    cudaMemPool_t pool = scratch_pool(t->device);
+    cudaMemPool_t pool = htex_scratch_pool(t->device);
     if (!pool) return HTEX_ERR_CUDA;
     void* scratch = nullptr;
     if (cudaMallocFromPoolAsync(&scratch, cnt_b + sq_b + pos_b + sout_b, pool, s) != cudaSuccess) {
@@ -462,7 +467,7 @@ htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int6
     htex_status st = HTEX_OK;
     for (int64_t c0 = 0; c0 < n && st == HTEX_OK; c0 += M) {
         const int64_t m = std::min<int64_t>(M, n - c0);
-        st = launch_sort<1>(t, P, words(q + c0), m, counters, words(sq), pos, 0, s);
+        st = launch_sort<1>(t, P, words(q + c0), m, counters, words(sq), pos, s);
         if (st == HTEX_OK) st = launch_fwd_dt<false>(t, FwdParams{sq, m, sout, d_status, nullptr}, fwd_flags, s);
         if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, t->num_sms, s);
     }
@@ -470,46 +475,48 @@ htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int6
     return st;
 }
 
+template <int C>
+htex_status launch_sort_rows(const htex_textures* t, const SortPlan& P, const htex_query* q, int64_t m,
+                             const float* g, uint32_t* counters, htex_query* sq, float* sg, cudaStream_t s) {
+    return launch_sort<1, C>(t, P, words(q), m, counters, words(sq), nullptr, s, g, sg);
+}
+
+// The adjoint on sorted queries: each chunk sorted by halfedge range with
+// its upstream gradient rows moving along (in the scatter's tiles, so they
+// leave in whole runs like the queries), then the warp-aggregated adjoint
+// over the sorted copy.
 htex_status htex_launch_backward_sorted(const htex_textures* t, const htex_query* q, int64_t n,
                                         const float* grad_out, float* grad_texels, htex_stream stream,
                                         int32_t* d_status) {
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (htex_bin_shift(t) < 0) return htex_launch_backward(t, q, n, grad_out, grad_texels, 0u, stream, d_status);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const SortPlan P = sort_plan(t->H);
     const int64_t M = std::min<int64_t>(n, kSortChunk);
     const size_t cnt_b = counter_bytes(P);
-    const size_t sq_b = size_t(M) * 16, pos_b = (size_t(M) * 4 + 255) & ~size_t(255);
-    const size_t g_b = size_t(M) * 4 * size_t(t->C);
-    cudaMemPool_t pool = scratch_pool(t->device);
+    const size_t sq_b = size_t(M) * 16, g_b = size_t(M) * 4 * size_t(t->C);
+    cudaMemPool_t pool = htex_scratch_pool(t->device);
     if (!pool) return HTEX_ERR_CUDA;
     void* scratch = nullptr;
-    if (cudaMallocFromPoolAsync(&scratch, cnt_b + sq_b + pos_b + g_b, pool, s) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&scratch, cnt_b + sq_b + g_b, pool, s) != cudaSuccess) {
         cudaGetLastError();
         return HTEX_ERR_OUT_OF_MEMORY;
     }
     uint8_t* base = static_cast<uint8_t*>(scratch);
     uint32_t* counters = reinterpret_cast<uint32_t*>(base);
     htex_query* sq = reinterpret_cast<htex_query*>(base + cnt_b);
-    int32_t* pos = reinterpret_cast<int32_t*>(base + cnt_b + sq_b);
-    float* gs = reinterpret_cast<float*>(base + cnt_b + sq_b + pos_b);
-    const unsigned g = unsigned(std::max(1, t->num_sms)) * 8;
+    float* gs = reinterpret_cast<float*>(base + cnt_b + sq_b);
     htex_status st = HTEX_OK;
     for (int64_t c0 = 0; c0 < n && st == HTEX_OK; c0 += M) {
         const int64_t m = std::min<int64_t>(M, n - c0);
-        st = launch_sort<1>(t, P, words(q + c0), m, counters, words(sq), pos, 0, s);
-        if (st != HTEX_OK) break;
         const float* gsrc = grad_out + c0 * t->C;
         switch (t->C) {
-        case 1: k_chunk_permute<1><<<g, 256, 0, s>>>(gsrc, pos, m, gs); break;
-        case 2: k_chunk_permute<2><<<g, 256, 0, s>>>(gsrc, pos, m, gs); break;
-        case 3: k_chunk_permute<3><<<g, 256, 0, s>>>(gsrc, pos, m, gs); break;
-        default: k_chunk_permute<4><<<g, 256, 0, s>>>(gsrc, pos, m, gs); break;
+        case 1: st = launch_sort_rows<1>(t, P, q + c0, m, gsrc, counters, sq, gs, s); break;
+        case 2: st = launch_sort_rows<2>(t, P, q + c0, m, gsrc, counters, sq, gs, s); break;
+        case 3: st = launch_sort_rows<3>(t, P, q + c0, m, gsrc, counters, sq, gs, s); break;
+        default: st = launch_sort_rows<4>(t, P, q + c0, m, gsrc, counters, sq, gs, s); break;
         }
-        if (cudaGetLastError() != cudaSuccess) {
-            st = HTEX_ERR_CUDA;
-            break;
-        }
-        st = htex_launch_backward(t, sq, m, gs, grad_texels, 0u, stream, d_status);
+        if (st == HTEX_OK)
+            st = htex_launch_backward(t, sq, m, gs, grad_texels, kBackwardAggregate, stream, d_status);
     }
     cudaFreeAsync(scratch, s);
     return st;
@@ -524,7 +531,7 @@ htex_status htex_launch_aniso_sorted(const htex_textures* t, const htex_query_an
     const size_t cnt_b = counter_bytes(P);
     const size_t sq_b = size_t(M) * sizeof(htex_query_aniso), pos_b = (size_t(M) * 4 + 255) & ~size_t(255);
     const size_t sout_b = size_t(M) * 4 * size_t(t->C);
-    cudaMemPool_t pool = scratch_pool(t->device);
+    cudaMemPool_t pool = htex_scratch_pool(t->device);
     if (!pool) return HTEX_ERR_CUDA;
     void* scratch = nullptr;
     if (cudaMallocFromPoolAsync(&scratch, cnt_b + sq_b + pos_b + sout_b, pool, s) != cudaSuccess) {
@@ -540,7 +547,7 @@ htex_status htex_launch_aniso_sorted(const htex_textures* t, const htex_query_an
     for (int64_t c0 = 0; c0 < n && st == HTEX_OK; c0 += M) {
         const int64_t m = std::min<int64_t>(M, n - c0);
         st = launch_sort<2>(t, P, reinterpret_cast<const int4*>(q + c0), m, counters, reinterpret_cast<int4*>(sq),
-                            pos, 0, s);
+                            pos, s);
         if (st == HTEX_OK) st = htex_launch_aniso(t, sq, m, kmax, sout, stream, d_status);
         if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, t->num_sms, s);
     }
@@ -558,14 +565,15 @@ extern "C" htex_status htex_queries_sort(const htex_textures* t, const htex_quer
         return HTEX_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const SortPlan P = sort_plan(t->H);
-    cudaMemPool_t pool = scratch_pool(t->device);
+    cudaMemPool_t pool = htex_scratch_pool(t->device);
     if (!pool) return HTEX_ERR_CUDA;
     void* counters = nullptr;
     if (cudaMallocFromPoolAsync(&counters, counter_bytes(P), pool, s) != cudaSuccess) {
         cudaGetLastError();
         return HTEX_ERR_OUT_OF_MEMORY;
     }
-    const htex_status st = launch_sort<1>(t, P, words(q), n, static_cast<uint32_t*>(counters), words(sorted), pos, 0, s);
+    const htex_status st =
+        launch_sort<1>(t, P, words(q), n, static_cast<uint32_t*>(counters), words(sorted), pos, s);
     cudaFreeAsync(counters, s);
     return st;
 }

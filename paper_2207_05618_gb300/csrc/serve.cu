@@ -8,9 +8,12 @@
 //   2. admits waiting requests: their asset is uploaded (asynchronously,
 //      from page-locked host memory) once it fits the budget, evicting the
 //      least recently used assets that no admitted request still needs;
-//   3. fills every free batch slot from the admitted requests in arrival
-//      order, at most 'request_chunk' queries of one request per batch, so
-//      requests that arrive while others run join the next batch;
+//   3. fills every free batch slot from the admitted requests, shortest
+//      remaining work first with ageing (a request's remaining query count
+//      shrinks with the time it has waited, so small requests overtake
+//      large ones and no request starves), at most 'request_chunk' queries
+//      of one request per batch, so requests that arrive while others run
+//      join the next batch;
 //   4. launches the batch: query copies in, the slot's graph (a memcpy node
 //      for the batch's descriptor table, then one persistent kernel per
 //      texel format whose blocks pull 4096-query tiles of any item through
@@ -335,8 +338,29 @@ bool admit(htex_server* s) {
     return progress;
 }
 
+// Order in which admitted requests fill a batch: shortest remaining work
+// first, aged -- a request's remaining query count is divided by
+// 1 + wait / kAgeScale, so small requests overtake large ones that arrived
+// earlier, and a large request that has waited moves forward until it is
+// served (no starvation).
+constexpr double kAgeScale = 1e-3;   // seconds
+
+void order_admitted(htex_server* s) {
+    const Clock::time_point now = Clock::now();
+    std::vector<std::pair<double, Request*>> keyed;
+    keyed.reserve(s->admitted.size());
+    for (Request* r : s->admitted) {
+        const double wait = std::chrono::duration<double>(now - r->t_submit).count();
+        keyed.emplace_back(double(r->n - r->issued) / (1.0 + wait / kAgeScale), r);
+    }
+    std::stable_sort(keyed.begin(), keyed.end(),
+                     [](const auto& x, const auto& y) { return x.first < y.first; });
+    for (size_t k = 0; k < keyed.size(); ++k) s->admitted[k] = keyed[k].second;
+}
+
 bool launch_batch(htex_server* s, Slot& sl) {
-    // requests in arrival order, at most request_chunk queries each
+    // requests by aged remaining work, at most request_chunk queries each
+    order_admitted(s);
     std::vector<std::pair<Request*, int64_t>> take;
     int64_t used = 0;
     for (Request* r : s->admitted) {

@@ -50,7 +50,60 @@ def parse_args():
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--no-extras", action="store_true", help="skip the precision and backward measurements")
     p.add_argument("--rows", type=int, default=460, help="cylinder rows (460: the asset-scale mesh)")
+    p.add_argument("--only", choices=["backward", "aniso", "cube"],
+                   help="run one workload alone (sorted adjoint on the differentiation workload; anisotropic "
+                        "lookups on the --rows asset with --queries queries; cube streaming), warm-up and timed "
+                        "launches only, and print its timing: for profiling one kernel")
     return p.parse_args()
+
+
+def run_only(args, hx, torch):
+    """One workload's launches alone (for ncu captures of one kernel)."""
+    import htex_synth as syn
+    stream = torch.cuda.current_stream()
+    if args.only == "backward":
+        fs, fv, V, _ = syn.uv_sphere()
+        mesh = hx.Mesh(fs, fv, V)
+        log2n = np.full(mesh.E, 5, np.int32)
+        tex = hx.Textures.upload(mesh, log2n, syn.texels_f32(log2n, 3, seed=2), 3, "f32", hx.BUILD_MIPS)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(4)
+        n = 2_000_000
+        q = device_queries(torch, mesh.H, n, gen)
+        g = torch.randn((n, 3), device="cuda", generator=gen)
+        grad = torch.zeros(tex.pool_elements, dtype=torch.float32, device="cuda")
+        fn = lambda: hx.lookup_backward(tex, q, g, grad_texels=grad, flags=hx.LOOKUP_BIN, stream=stream)
+        units = n
+    elif args.only == "aniso":
+        fs, fv, V, _ = syn.cylinder(rows=args.rows)
+        mesh = hx.Mesh(fs, fv, V)
+        log2n = np.full(mesh.E, 6, np.int32)
+        tex = hx.Textures.upload(mesh, log2n, syn.texels_u8(log2n, 4, seed=21), 4, "u8", hx.BUILD_MIPS)
+        r = aniso_bench(hx, torch, stream, mesh, tex, n=args.queries, reps=args.steps, warm=args.warmup,
+                        sorted_too=False)
+        print(json.dumps({"only": "aniso", **r}), flush=True)
+        return
+    else:
+        fs, fv, V, _ = syn.cube()
+        mesh = hx.Mesh(fs, fv, V)
+        log2n = np.full(mesh.E, 4, np.int32)
+        tex = hx.Textures.upload(mesh, log2n, syn.texels_f32(log2n, 4, seed=1), 4, "f32", hx.BUILD_MIPS)
+        n = 1 << 24
+        q = torch.from_numpy(hx.pack_queries(*syn.queries(mesh.H, n, seed=2))).cuda()
+        out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        fn = lambda: hx.lookup(tex, q, out=out, stream=stream)
+        units = n
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    print(json.dumps({"only": args.only, "ms": ms, "units_per_s": units / (ms / 1e3)}), flush=True)
 
 
 # ----------------------------------------------------------------- workload
@@ -131,6 +184,39 @@ def profiled_traffic(kernel: str):
     if m and t and m.group(1) == filter_source_hash():
         return float(t.group(1))
     return None
+
+
+# the files the anisotropic kernel and the adjoint are compiled from (and the build flags)
+ANISO_SOURCES = ("csrc/aniso.cu", "csrc/aniso_launch.h", "csrc/fetch.cuh", "csrc/htex_internal.h", "build.py")
+BACKWARD_SOURCES = ("csrc/backward.cu", "csrc/fetch.cuh", "csrc/htex_internal.h", "build.py")
+
+
+def sources_hash(rels) -> str:
+    h = hashlib.sha256()
+    for rel in rels:
+        with open(os.path.join(ROOT, "paper_2207_05618_gb300", rel), "rb") as fh:
+            h.update(rel.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def profiled_values(name: str, rels):
+    """'key: value' numbers of a committed ncu summary, when its
+    source_files_hash matches the current sources of the kernel; else None."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_files_hash:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != sources_hash(rels):
+        return None
+    vals = {}
+    for k, v in re.findall(r"^(\w+):\s*(\S+)\s*$", text, flags=re.M):
+        try:
+            vals[k] = float(v)
+        except ValueError:
+            pass
+    return vals
 
 
 def hbm_peak():
@@ -369,6 +455,9 @@ def main():
     if dist:
         dist.barrier()
     import paper_2207_05618_gb300 as hx
+    if args.only:
+        run_only(args, hx, torch)
+        return
 
     nq = args.queries
     fs, fv, V, positions, qs = asset_inputs(rank, nq, args.rows)
@@ -465,6 +554,7 @@ def main():
     serving = None if args.no_serving else serving_bench(hx, torch)
     frame = None if args.no_extras else frame_bench(hx, torch, stream, mesh, tex, positions, args.rows)
     precision = None if args.no_extras else precision_bench(hx, torch, stream)
+    precision_asset = None if args.no_extras else precision_asset_bench(hx, torch, stream)
     backward = None if args.no_extras else backward_bench(hx, torch, stream)
     aniso = None if args.no_extras else aniso_bench(hx, torch, stream, mesh, tex)
 
@@ -510,24 +600,33 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * launches_per_step, "step_ms_stages": stages,
             "cube_stream": cube, "serving": serving,
-            "precision": precision, "backward": backward, "frame": frame, "aniso": aniso,
+            "precision": precision, "precision_asset": precision_asset, "backward": backward, "frame": frame, "aniso": aniso,
             "source_hash": source_hash(),
         }), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7):
+SERVER_CONFIG = {"batch_queries": 1 << 22, "batch_slots": 3, "max_items": 256, "request_chunk": 1 << 20}
+
+
+def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7, repeats: int = 3, server_configs=None):
     """The serving workload: 8 resident assets (halfedges log-spaced over
     [1k, 500k], 128^2..16^2 RGBA8 / FP16 textures), a Poisson stream of
     requests of log-uniform 1k..4M queries with uniform asset tags, offered
-    at 'load' times the server's own back-to-back throughput under a device
-    budget of 60% of the assets' bytes.  Reports p50/p99 latency and
-    aggregate lookups/s for the server at that budget and with every asset
-    resident, and, on the same arrivals, for the plain path (one
-    htex_lookup_host per request in arrival order, all assets resident)."""
+    at 'load' times the plain path's back-to-back throughput (one
+    htex_lookup_host per request, requests back to back: a fixed measure of
+    what the device and the host link deliver), under a device budget of 60%
+    of the assets' bytes.  For each of 'repeats' arrival streams (different
+    seeds): p50/p99 latency and aggregate lookups/s for the server at that
+    budget and with every asset resident, and, on the same arrivals, for the
+    plain path (one htex_lookup_host per request in arrival order, all
+    assets resident).  Reports the median over the streams and every
+    stream's figures; with a list of server configurations, one such result
+    per configuration (the same streams)."""
     import htex_synth as syn
     from paper_2207_05618_gb300 import serve
+    cfgs = [dict(SERVER_CONFIG, **c) for c in (server_configs or [{}])]
     specs = syn.serving_assets()
     assets = []
     for a in specs:
@@ -553,7 +652,7 @@ def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7):
         off = int(rng.integers(0, qmax - n + 1))
         return qpool[a].data_ptr() + off * 16
 
-    # plain path throughput, requests back to back
+    # plain path throughput, requests back to back (sets the offered load)
     _, sizes, tags = syn.poisson_requests(n_requests, 1.0, len(assets), seed=11)
     stream = torch.cuda.current_stream()
     warm = min(50, n_requests)
@@ -567,40 +666,20 @@ def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7):
         hx.lookup_host(assets[tags[k]]["alone"], qpool[tags[k]][:n], out=out_arena[:n], stream=stream)
     torch.cuda.synchronize()
     plain_rate = float(sizes.sum()) / (time.perf_counter() - t)
+    rate = load * plain_rate / float(sizes.mean())
+    pct = lambda x, p: float(np.percentile(x, p) * 1e3)
 
-    def new_server(budget):
-        server = serve.Server(int(budget), batch_queries=1 << 22, batch_slots=3, max_items=256,
-                              request_chunk=1 << 20)
+    def new_server(cfg, budget):
+        server = serve.Server(int(budget), **cfg)
         for a in assets:
             server.add_asset(a["mesh"], a["log2n"], a["pool"], a["scales"], 4, a["dtype"])
         return server
 
-    # the server's capacity at the 60% budget: the same requests, all at once (sets the offered load)
-    server = new_server(0.6 * total)
-    _, cap_wall = serve.replay(server, np.zeros(n_requests), sizes, tags, qsrc, lambda k, a, n: out_arena.data_ptr())
-    server.close()
-    server_rate = float(sizes.sum()) / cap_wall
-    rate = load * server_rate / float(sizes.mean())
-    arrivals, sizes, tags = syn.poisson_requests(n_requests, rate, len(assets), seed=12)
-
-    # the plain path on these arrivals: one request at a time, first come first served
-    lat_plain = np.zeros(n_requests)
-    t0 = time.perf_counter()
-    for k in range(n_requests):
-        while time.perf_counter() < t0 + arrivals[k]:
-            pass
-        n = int(sizes[k])
-        hx.lookup_host(assets[tags[k]]["alone"], qpool[tags[k]][:n], out=out_arena[:n], stream=stream)
-        stream.synchronize()
-        lat_plain[k] = time.perf_counter() - (t0 + arrivals[k])
-    wall_plain = time.perf_counter() - t0
-    for a in assets:
-        a["alone"].close()
-
-    pct = lambda x, p: float(np.percentile(x, p) * 1e3)
-
-    def run_server(budget):
-        server = new_server(budget)
+    def run_server(cfg, budget, arrivals, sizes, tags):
+        server = new_server(cfg, budget)
+        # warm-up: one small request per asset, served before the timed stream
+        serve.replay(server, np.zeros(len(assets)), np.full(len(assets), 1024), np.arange(len(assets)), qsrc,
+                     lambda k, a, n: out_arena.data_ptr())
         lat, wall = serve.replay(server, arrivals, sizes, tags, qsrc, lambda k, a, n: out_arena.data_ptr())
         st = server.stats()
         server.close()
@@ -608,16 +687,49 @@ def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7):
                 "lookups_per_s": float(sizes.sum()) / wall, "batches": st["batches"], "uploads": st["uploads"],
                 "evictions": st["evictions"]}
 
-    res = run_server(0.6 * total)
-    res.update({"requests": int(n_requests), "offered_load": load,
-                "offered_lookups_per_s": float(rate * sizes.mean()),
-                "server_back_to_back_lookups_per_s": server_rate, "assets": len(assets),
-                "asset_bytes": int(total),
-                "all_resident": run_server(2 * total),
-                "plain_path": {"p50_ms": pct(lat_plain, 50), "p99_ms": pct(lat_plain, 99),
-                               "lookups_per_s": float(sizes.sum()) / wall_plain,
-                               "back_to_back_lookups_per_s": plain_rate, "all_resident": True}})
-    return res
+    def run_plain(arrivals, sizes, tags):
+        # one request at a time, first come first served
+        lat = np.zeros(n_requests)
+        t0 = time.perf_counter()
+        for k in range(n_requests):
+            while time.perf_counter() < t0 + arrivals[k]:
+                pass
+            n = int(sizes[k])
+            hx.lookup_host(assets[tags[k]]["alone"], qpool[tags[k]][:n], out=out_arena[:n], stream=stream)
+            stream.synchronize()
+            lat[k] = time.perf_counter() - (t0 + arrivals[k])
+        wall = time.perf_counter() - t0
+        return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "lookups_per_s": float(sizes.sum()) / wall}
+
+    streams = [syn.poisson_requests(n_requests, rate, len(assets), seed=12 + r) for r in range(repeats)]
+    plain = [run_plain(*st) for st in streams]
+    results = []
+    for cfg in cfgs:
+        # the server's back-to-back capacity at the budget (the same requests, all at once)
+        server = new_server(cfg, 0.6 * total)
+        _, cap_wall = serve.replay(server, np.zeros(n_requests), sizes, tags, qsrc,
+                                   lambda k, a, n: out_arena.data_ptr())
+        server.close()
+        runs = [{"budget": run_server(cfg, 0.6 * total, *st), "all_resident": run_server(cfg, 2 * total, *st),
+                 "plain_path": pl} for st, pl in zip(streams, plain)]
+        med = lambda key, sub: float(np.median([x[key][sub] for x in runs]))
+        res = {"requests": int(n_requests), "repeats": repeats, "offered_load": load,
+               "offered_lookups_per_s": float(rate * sizes.mean()), "plain_back_to_back_lookups_per_s": plain_rate,
+               "server_back_to_back_lookups_per_s": float(sizes.sum()) / cap_wall,
+               "assets": len(assets), "asset_bytes": int(total), "server_config": cfg,
+               "budget_bytes": int(0.6 * total)}
+        for key in ("budget", "all_resident", "plain_path"):
+            res[key] = {"p50_ms": med(key, "p50_ms"), "p99_ms": med(key, "p99_ms"),
+                        "lookups_per_s": med(key, "lookups_per_s"),
+                        "p99_ms_each_stream": [x[key]["p99_ms"] for x in runs],
+                        "p50_ms_each_stream": [x[key]["p50_ms"] for x in runs]}
+        res["budget"]["uploads_each_stream"] = [x["budget"]["uploads"] for x in runs]
+        res["budget"]["batches_each_stream"] = [x["budget"]["batches"] for x in runs]
+        res["all_resident"]["batches_each_stream"] = [x["all_resident"]["batches"] for x in runs]
+        results.append(res)
+    for a in assets:
+        a["alone"].close()
+    return results if server_configs else results[0]
 
 
 def device_queries(torch, H, n, gen, footprint=False):
@@ -635,8 +747,8 @@ def device_queries(torch, H, n, gen, footprint=False):
     return q
 
 
-def timed(torch, stream, fn, reps):
-    for _ in range(3):
+def timed(torch, stream, fn, reps, warm=3):
+    for _ in range(warm):
         fn()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -693,10 +805,48 @@ def precision_bench(hx, torch, stream):
     return res
 
 
-def aniso_bench(hx, torch, stream, mesh, tex, n=1 << 22):
+def precision_asset_bench(hx, torch, stream, rows: int = 115, nq: int = 1 << 22):
+    """Reduced-precision texels where the filter is DRAM-bound: the asset
+    mesh recipe at a quarter of its rows (115: about 130k halfedges, the
+    asset's density of queries per texture), 64x64 RGBA textures with mip
+    chains stored as FP32, FP16, E4M3 (per-texture scale 1) and RGBA8,
+    4,194,304 queries with the workload's footprints, sorted
+    (HTEX_LOOKUP_BIN).  Texel codes are random (a timing workload: each
+    format's error against the FP64 oracle is measured on the cube)."""
+    import htex_synth as syn
+    fs, fv, V, _ = syn.cylinder(rows=rows)
+    mesh = hx.Mesh(fs, fv, V)
+    log2n = np.full(mesh.E, 6, np.int32)
+    q = torch.from_numpy(hx.pack_queries(*syn.queries(mesh.H, nq, seed=5, footprint="loguniform"))).cuda()
+    out = torch.empty((nq, 4), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(77)
+    res = {"halfedges": mesh.H, "edges": mesh.E, "queries": nq}
+    for fmt in ("f32", "f16", "e4m3", "u8"):
+        total, _ = hx.Textures.layout(mesh, log2n, 4, fmt)
+        if fmt == "f32":
+            pool = rng.random(total // 4, dtype=np.float32).view(np.uint8)
+        elif fmt == "f16":
+            pool = rng.random(total // 2, dtype=np.float32).astype(np.float16).view(np.uint8)
+        elif fmt == "e4m3":
+            pool = rng.integers(0, 0x7f, total, dtype=np.uint8)      # finite non-negative codes
+        else:
+            pool = np.frombuffer(rng.bytes(total), np.uint8)
+        tex = hx.Textures.upload_pool(mesh, log2n, pool, np.ones(mesh.E, np.float32), 4, fmt)
+        del pool
+        ms = timed(torch, stream, lambda: hx.lookup(tex, q, out=out, flags=hx.LOOKUP_BIN, stream=stream), 20)
+        res[fmt] = {"lookups_per_s": nq / (ms / 1e3), "ms": ms, "pool_bytes": tex.pool_bytes,
+                    "texel_bytes": 4 * {"f32": 4, "f16": 2, "e4m3": 1, "u8": 1}[fmt]}
+        tex.close()
+    return res
+
+
+def aniso_bench(hx, torch, stream, mesh, tex, n=1 << 22, reps=10, warm=3, sorted_too=True):
     """Anisotropic lookups on the asset-scale textures: major axis
     log-uniform 2^-8..1 quad widths, anisotropy log-uniform 1..16, uniform
-    direction, at most 16 probes."""
+    direction, at most 16 probes.  The kernel is bound by instruction issue,
+    not DRAM: its roofline entry gives the DRAM bytes per lookup and the
+    issue activity from the committed ncu summary (while the kernel's
+    sources are unchanged), the live time, and the DRAM rate they imply."""
     import htex_synth as syn
     h, u, v, _ = syn.queries(mesh.H, n, seed=31)
     rng = np.random.default_rng(32)
@@ -709,14 +859,43 @@ def aniso_bench(hx, torch, stream, mesh, tex, n=1 << 22):
     k = np.minimum(np.ceil(np.sqrt(np.maximum(px2, py2) / np.minimum(px2, py2))), 16)
     q = torch.from_numpy(hx.pack_queries_aniso(h, u, v, *d)).cuda()
     out = torch.empty((n, 4), dtype=torch.float32, device="cuda")
-    for _ in range(3):
+    for _ in range(warm):
         hx.lookup_aniso(tex, q, 16, out=out, stream=stream)
-    ms = timed(torch, stream, lambda: hx.lookup_aniso(tex, q, 16, out=out, stream=stream), 10)
-    sorted_ms = timed(torch, stream, lambda: hx.lookup_aniso(tex, q, 16, out=out, stream=stream,
-                                                             flags=hx.LOOKUP_BIN), 10)
+    ms = timed(torch, stream, lambda: hx.lookup_aniso(tex, q, 16, out=out, stream=stream), reps, warm=0)
+    sorted_ms = (timed(torch, stream, lambda: hx.lookup_aniso(tex, q, 16, out=out, stream=stream,
+                                                              flags=hx.LOOKUP_BIN), reps) if sorted_too else None)
+    prof = profiled_values("lookup_aniso.md", ANISO_SOURCES)
+    peak, _ = hbm_peak()
+    roof = {"bound": "instruction issue", "unit": "GB/s", "peak": peak}
+    if prof:
+        b = prof["aniso_dram_bytes_per_lookup"]
+        roof.update({"dram_bytes_per_lookup": b, "achieved": b * n / (ms / 1e3) / 1e9,
+                     "frac": b * n / (ms / 1e3) / 1e9 / peak, "issue_active_pct": prof.get("aniso_issue_active_pct"),
+                     "source": "profiles/lookup_aniso.md (ncu, quarter-size asset)"})
     return {"queries": n, "max_aniso": 16, "mean_probes": float(k.mean()), "ms": ms,
             "lookups_per_s": n / (ms / 1e3), "probes_per_s": float(k.sum()) / (ms / 1e3),
-            "sorted_ms": sorted_ms, "sorted_lookups_per_s": n / (sorted_ms / 1e3)}
+            "sorted_ms": sorted_ms, "sorted_lookups_per_s": n / (sorted_ms / 1e3) if sorted_ms else None,
+            "roofline": roof}
+
+
+def backward_roofline(taps, bwd_bytes, n, call_ms, peak):
+    """The sorted adjoint against HBM: algorithmic bytes (query, gradient
+    row, one C-float atomic add per tap) over the whole sorted call's time,
+    and, while the committed ncu summary matches the kernel's sources, the
+    DRAM bytes the kernel moves per query."""
+    r = {"bound": "L2 atomics + hbm (latency-bound: see profiles/backward_differentiation.md)", "unit": "GB/s",
+         "peak": peak, "mean_taps": taps, "algorithmic_bytes_per_query": bwd_bytes,
+         "achieved": bwd_bytes * n / (call_ms / 1e3) / 1e9,
+         "frac": bwd_bytes * n / (call_ms / 1e3) / 1e9 / peak,
+         "atomic_adds_per_s": taps * n / (call_ms / 1e3),
+         "note": "whole htex_lookup_backward call with HTEX_LOOKUP_BIN (range sort carrying the gradient rows, "
+                 "then the warp-aggregated adjoint)"}
+    prof = profiled_values("backward_differentiation.md", BACKWARD_SOURCES)
+    if prof:
+        b = prof["backward_dram_bytes_per_query"]
+        r["dram"] = {"bytes_per_query": b, "achieved": b * n / (call_ms / 1e3) / 1e9,
+                     "frac": b * n / (call_ms / 1e3) / 1e9 / peak}
+    return r
 
 
 def backward_bench(hx, torch, stream):
@@ -777,12 +956,7 @@ def backward_bench(hx, torch, stream):
             "forward_sorted_lookups_per_s": n / (fwd_sorted_ms / 1e3),
             "backward_sorted_queries_per_s": n / (bwd_sorted_ms / 1e3),
             "backward_ms": bwd_ms, "backward_sorted_ms": bwd_sorted_ms,
-            "roofline": {"bound": "L2 atomics + hbm", "mean_taps": taps, "algorithmic_bytes_per_query": bwd_bytes,
-                         "achieved_gbs_sorted_call": bwd_bytes * n / (bwd_sorted_ms / 1e3) / 1e9,
-                         "peak_gbs": peak,
-                         "frac_sorted_call": bwd_bytes * n / (bwd_sorted_ms / 1e3) / 1e9 / peak,
-                         "atomic_adds_per_s_sorted_call": taps * n / (bwd_sorted_ms / 1e3),
-                         "note": "whole htex_lookup_backward call (sort by texture + adjoint)"},
+            "roofline": backward_roofline(taps, bwd_bytes, n, bwd_sorted_ms, peak),
             "fit": {"steps": r.steps, "initial_loss": r.losses[0], "final_loss": r.losses[-1],
                     "final_over_initial": r.ratio, "ms_per_step": r.seconds * 1e3 / r.steps,
                     "stages": stages, "loss_every_20": r.losses[::20]}}

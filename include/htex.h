@@ -278,8 +278,10 @@ htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, 
  *   q          device [n] htex_query_aniso (16-byte aligned)
  *   max_aniso  1..16
  *   flags      HTEX_LOOKUP_BIN: sort the queries by halfedge range first,
- *              as htex_lookup does (same results; scratch of 36 + 4 *
- *              channels bytes per chunk query)
+ *              as htex_lookup does (same results, bit for bit: each
+ *              query's probes are summed in probe order whatever queries
+ *              share its warp; scratch of 36 + 4 * channels bytes per
+ *              chunk query)
  *   out        device [n][channels] float (alignment as htex_lookup)
  *   d_status   device int32, nullable: incremented once per invalid query
  *              (h out of range, non-finite u, v or derivative, or an

@@ -18,9 +18,18 @@
 //     Alg. 2, with full 2x2 zero-bordered taps (a probe off the triangle can
 //     reach any texel of the neighbouring quads); the result is the summed
 //     data over the summed normalisation weight.
-// One thread per query, grid-stride.  A fetch whose quad no probe of any
-// lane of the warp can reach (more than half a coarsest-level texel
-// outside it) is skipped warp-uniformly.
+// Work distribution: a warp takes 32 queries at a time and works through
+// all of their probes together, 32 (query, probe) pairs per round, so a
+// warp whose lanes need 1 to 16 probes runs ceil(sum K / 32) rounds instead
+// of its largest K.  Each query's constants (centre, scaled major axis, K,
+// and for each fetch its two levels' offsets, sizes and weights, code
+// factor and reflection) are computed once by its own lane and kept in
+// shared memory for the lanes that run its probes; each round's probe
+// results (data and weight sums) go through shared memory back to the
+// lanes of their queries, which add them in probe order, so that a query's
+// result does not depend on which other queries share its warp.  A fetch whose
+// quad no probe of the round can reach (more than half a coarsest-level
+// texel outside it) is skipped warp-uniformly.
 #include <cuda_runtime.h>
 
 #include "lookup_core.cuh"
@@ -52,15 +61,15 @@ __device__ __forceinline__ TapsG taps_g(float p, int N) {
 }
 
 // Per-query constants of one fetch, fixed over its probes: where its two
-// levels start, their sizes and weights, how far outside the quad a probe
-// can still reach an in-bounds tap (half a texel of the coarsest level
-// read), the code factor and the Alg. 2 reflection.
+// levels start, their sizes and weights, the code factor and the Alg. 2
+// reflection.
 struct FetchConst {
-    int64_t base0, base1;   // byte offsets of texel (0, 0) of levels l0 and l1
-    int N0, N1;             // their sizes (l1 = l0 when one level is read)
+    int64_t base0;          // byte offset of texel (0, 0) of level l0
+    int32_t d1;             // byte offset of level l1 from level l0 (0 when one level is read)
+    int16_t n0, n1;         // log2 of their sizes (l1 = l0 when one level is read)
     float w0, w1;           // their weights (w1 = 0 when one level is read)
-    float half, sc;
-    bool flip, two;
+    float sc;               // code factor
+    uint32_t flip;          // Alg. 2 reflection
 };
 
 template <int DT, int C>
@@ -68,14 +77,12 @@ __device__ __forceinline__ FetchConst fetch_const(const TexRef& t, const Lod& d,
     constexpr int TB = C * Fmt<DT>::ES;
     FetchConst f;
     const int l1 = d.l1 >= 0 ? d.l1 : d.l0;
-    f.N0 = 1 << (t.n - d.l0);
-    f.N1 = 1 << (t.n - l1);
+    f.n0 = int16_t(t.n - d.l0);
+    f.n1 = int16_t(t.n - l1);
     f.base0 = int64_t(t.off) + int64_t(level_texels(t.n, d.l0)) * TB;
-    f.base1 = int64_t(t.off) + int64_t(level_texels(t.n, l1)) * TB;
-    f.two = d.l1 >= 0;
+    f.d1 = int32_t(int64_t(level_texels(t.n, l1) - level_texels(t.n, d.l0)) * TB);
     f.w0 = d.w0;
-    f.w1 = f.two ? d.w1 : 0.0f;
-    f.half = 0.5f / float(f.N1);
+    f.w1 = d.l1 >= 0 ? d.w1 : 0.0f;
     f.sc = code_factor<DT>(t);
     f.flip = code & kFlipBit;
     return f;
@@ -105,14 +112,16 @@ __device__ __forceinline__ void aniso_level(const Asset<GlobalSpace>& A, int64_t
 // One fetch of one probe (one or two levels), skipped when no lane of the
 // warp has a tap in bounds.
 template <int DT, int C>
-__device__ __forceinline__ void aniso_fetch(const Asset<GlobalSpace>& A, unsigned act, bool ok, const FetchConst& f,
-                                            float a, float b, float (&acc)[C], float& W) {
+__device__ __forceinline__ void aniso_fetch(const Asset<GlobalSpace>& A, bool on, const FetchConst& f, float a,
+                                            float b, float (&acc)[C], float& W) {
     const float x = f.flip ? 1.0f - a : a, y = f.flip ? 1.0f - b : b;
-    const bool near = ok && x > -f.half && x < 1.0f + f.half && y > -f.half && y < 1.0f + f.half;
-    if (!__any_sync(act, near)) return;
-    aniso_level<DT, C>(A, f.base0, f.N0, x, y, near ? f.w0 : 0.0f, f.sc, acc, W);
-    if (__any_sync(act, near && f.two))
-        aniso_level<DT, C>(A, f.base1, f.N1, x, y, (near && f.two) ? f.w1 : 0.0f, f.sc, acc, W);
+    const float half = 0.5f / float(1 << f.n1);
+    const bool near = on && x > -half && x < 1.0f + half && y > -half && y < 1.0f + half;
+    if (!__any_sync(0xffffffffu, near)) return;
+    aniso_level<DT, C>(A, f.base0, 1 << f.n0, x, y, near ? f.w0 : 0.0f, f.sc, acc, W);
+    const bool two = near && f.w1 != 0.0f;
+    if (__any_sync(0xffffffffu, two))
+        aniso_level<DT, C>(A, f.base0 + f.d1, 1 << f.n1, x, y, two ? f.w1 : 0.0f, f.sc, acc, W);
 }
 
 // Probe count (see the file comment): same float operations as the oracle.
@@ -124,69 +133,136 @@ __device__ __forceinline__ int aniso_probes(float px2, float py2, int kmax) {
     return max(1, int(ceilf(r)));
 }
 
+constexpr int kAnisoThreads = 256;
+constexpr int kAnisoWarps = kAnisoThreads / 32;
+constexpr int kAnisoMaxK = 16;
+
+// One query's constants, written by its lane, read by the lanes that run
+// its probes.
+struct AnisoQuery {
+    float u, v, mu, mv;     // centre and the probe spacing axis (major axis times s)
+    int32_t K;              // probes (0: the lane holds no query)
+    int32_t ok;             // a valid query
+    FetchConst f[3];        // own, Next, Prev
+};
+
 template <int DT, int C>
-__global__ void __launch_bounds__(256) k_lookup_aniso(Asset<GlobalSpace> A, AnisoParams p) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        const int4 r0 = ld_query(reinterpret_cast<const htex_query*>(p.q), 2 * i);
-        const int4 r1 = ld_query(reinterpret_cast<const htex_query*>(p.q), 2 * i + 1);
+__global__ void __launch_bounds__(kAnisoThreads) k_lookup_aniso(Asset<GlobalSpace> A, AnisoParams p) {
+    __shared__ AnisoQuery sq[kAnisoWarps][32];
+    __shared__ uint8_t owner[kAnisoWarps][32 * kAnisoMaxK];   // the query lane of each of the warp's probes
+    __shared__ float pr[kAnisoWarps][C + 1][32];             // one round's probe results: data and weight sums
+    const unsigned lane = threadIdx.x & 31u, wib = threadIdx.x >> 5;
+    const int64_t warps = int64_t(gridDim.x) * kAnisoWarps;
+    for (int64_t base = (int64_t(blockIdx.x) * kAnisoWarps + wib) * 32; base < p.n; base += warps * 32) {
+        // ---- this lane's query: decode, probe count, per-fetch constants
+        const int64_t i = base + lane;
+        const bool valid = i < p.n;
+        const int4 r0 = valid ? ld_query(reinterpret_cast<const htex_query*>(p.q), 2 * i) : make_int4(-1, 0, 0, 0);
+        const int4 r1 = valid ? ld_query(reinterpret_cast<const htex_query*>(p.q), 2 * i + 1) : make_int4(0, 0, 0, 0);
         const float dudx = __int_as_float(r1.x), dvdx = __int_as_float(r1.y);
         const float dudy = __int_as_float(r1.z), dvdy = __int_as_float(r1.w);
         const float px2 = __fadd_rn(__fmul_rn(dudx, dudx), __fmul_rn(dvdx, dvdx));
         const float py2 = __fadd_rn(__fmul_rn(dudy, dudy), __fmul_rn(dvdy, dvdy));
         int h;
         float u, v, f;
-        bool ok = decode_query(make_int4(r0.x, r0.y, r0.z, 0), A.H, h, u, v, f);
+        bool ok = valid && decode_query(make_int4(r0.x, r0.y, r0.z, 0), A.H, h, u, v, f);
         ok = ok && isfinite(dudx) && isfinite(dvdx) && isfinite(dudy) && isfinite(dvdy) && isfinite(px2) &&
              isfinite(py2);
         if (!ok) {
             u = 0.0f;
             v = 0.0f;
-            if (p.status) atomicAdd(p.status, 1);
+            if (valid && p.status) atomicAdd(p.status, 1);
         }
-        const int K = ok ? aniso_probes(px2, py2, p.kmax) : 1;
+        const int K = valid ? (ok ? aniso_probes(px2, py2, p.kmax) : 1) : 0;
         const bool major_y = py2 > px2;
         const float pmax = sqrtf(fmaxf(px2, py2));
-        const float s = pmax > float(K) ? float(K) / pmax : 1.0f;
-        const float mu = (major_y ? dudy : dudx) * s, mv = (major_y ? dvdy : dvdx) * s;
+        const float s = pmax > float(max(K, 1)) ? float(K) / pmax : 1.0f;
         const float lf = footprint_log2(ok ? pmax / float(K) : 0.0f);
-
         const uint4 rec = ok ? A.rec.ld16(uint64_t(h) * 16u) : make_uint4(0, 0, 0, 0);
         const TexRef to = tex_ref<DT>(A, rec.x & ~kFlipBit);
         const TexRef tn = tex_ref<DT>(A, rec.y & ~kFlipBit);
         const TexRef tp = tex_ref<DT>(A, rec.z & ~kFlipBit);
-        const FetchConst f0 = fetch_const<DT, C>(to, select_lod(lf, to.n), rec.x);
-        const FetchConst f1 = fetch_const<DT, C>(tn, select_lod(lf, tn.n), rec.y);
-        const FetchConst f2 = fetch_const<DT, C>(tp, select_lod(lf, tp.n), rec.z);
+        AnisoQuery& Q = sq[wib][lane];
+        Q.u = u;
+        Q.v = v;
+        Q.mu = (major_y ? dudy : dudx) * s;
+        Q.mv = (major_y ? dvdy : dvdx) * s;
+        Q.K = K;
+        Q.ok = ok;
+        Q.f[0] = fetch_const<DT, C>(to, select_lod(lf, to.n), rec.x);
+        Q.f[1] = fetch_const<DT, C>(tn, select_lod(lf, tn.n), rec.y);
+        Q.f[2] = fetch_const<DT, C>(tp, select_lod(lf, tp.n), rec.z);
+        float qacc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) qacc[c] = 0.0f;
+        float qW = 0.0f;
 
-        float acc[C];
+        // ---- the warp's probes in order: query lane by lane, probe by probe
+        int incl = K;
 #pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = 0.0f;
-        float W = 0.0f;
-        const unsigned act = __activemask();
-        const int Kw = int(__reduce_max_sync(act, unsigned(K)));   // the warp walks its lanes' largest K
-        for (int k = 0; k < Kw; ++k) {
-            const bool on = ok && k < K;
-            const float t = (float(2 * k + 1) - float(K)) / float(2 * K);
-            const float pu = fmaf(mu, t, u), pv = fmaf(mv, t, v);
-            aniso_fetch<DT, C>(A, act, on, f0, pu, pv, acc, W);
-            aniso_fetch<DT, C>(A, act, on, f1, pv, -pu, acc, W);
-            aniso_fetch<DT, C>(A, act, on, f2, -pv, pu, acc, W);
+        for (int d = 1; d < 32; d <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= unsigned(d)) incl += o;
         }
-        // invalid queries (W = 0, acc = 0): 0 * inf = NaN, as in the isotropic lookup
-        const float inv = __frcp_rn(W);
-        float r[C];
+        const int first = incl - K;                          // this lane's first probe
+        const int P = __shfl_sync(0xffffffffu, incl, 31);     // the warp's probes
+        for (int k = 0; k < K; ++k) owner[wib][first + k] = uint8_t(lane);
+        __syncwarp();
+
+        for (int r0p = 0; r0p < P; r0p += 32) {
+            const int j = r0p + int(lane);
+            const bool has = j < P;
+            const int q = has ? owner[wib][j] : int(owner[wib][P - 1]);
+            const int qfirst = __shfl_sync(0xffffffffu, first, q);
+            const AnisoQuery& R = sq[wib][q];
+            const bool on = has && R.ok;
+            const int KR = R.K, k = j - qfirst;
+            const float t = (float(2 * k + 1) - float(KR)) / float(2 * KR);
+            const float pu = fmaf(R.mu, t, R.u), pv = fmaf(R.mv, t, R.v);
+            float acc[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) r[c] = acc[c] * inv;
-        store_out<C>(p.out, i, r);
+            for (int c = 0; c < C; ++c) acc[c] = 0.0f;
+            float W = 0.0f;
+            aniso_fetch<DT, C>(A, on, R.f[0], pu, pv, acc, W);
+            aniso_fetch<DT, C>(A, on, R.f[1], pv, -pu, acc, W);
+            aniso_fetch<DT, C>(A, on, R.f[2], -pv, pu, acc, W);
+#pragma unroll
+            for (int c = 0; c < C; ++c) pr[wib][c][lane] = acc[c];
+            pr[wib][C][lane] = W;
+            __syncwarp();
+            // each lane adds the probes of its own query that this round
+            // computed, in probe order: the same sums whatever the other
+            // queries of the warp are
+            const int a = max(first, r0p) - r0p, b = min(first + K, r0p + 32) - r0p;
+            for (int m = a; m < b; ++m) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) qacc[c] += pr[wib][c][m];
+                qW += pr[wib][C][m];
+            }
+            __syncwarp();
+        }
+
+        // ---- normalise and store (invalid queries: W = 0, data 0, 0 * inf = NaN)
+        if (valid) {
+            const float inv = __frcp_rn(qW);
+            float res[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) res[c] = qacc[c] * inv;
+            store_out<C>(p.out, i, res);
+        }
+        __syncwarp();
     }
 }
 
 template <int DT, int C>
 htex_status launch_aniso_c(const htex_textures* t, const AnisoParams& p, cudaStream_t s) {
-    const int64_t want = (p.n + 255) / 256;
-    const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * 8);
-    k_lookup_aniso<DT, C><<<unsigned(grid), 256, 0, s>>>(global_asset(t), p);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_lookup_aniso<DT, C>, kAnisoThreads, 0) != cudaSuccess ||
+        b < 1)
+        b = 1;
+    const int64_t want = (p.n + kAnisoThreads - 1) / kAnisoThreads;
+    const int64_t grid = std::min<int64_t>(want, int64_t(t->num_sms) * b);
+    k_lookup_aniso<DT, C><<<unsigned(grid), kAnisoThreads, 0, s>>>(global_asset(t), p);
     return cudaGetLastError() == cudaSuccess ? HTEX_OK : HTEX_ERR_CUDA;
 }
 

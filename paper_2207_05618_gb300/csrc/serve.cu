@@ -477,6 +477,20 @@ void run(htex_server* s) {
         for (Slot& sl : s->slots)
             if (!sl.busy) progress |= launch_batch(s, sl);
         if (!progress) {
+            // idle time: instantiate the graphs of slots whose format set is
+            // stale, so that the first batches after new assets do not wait
+            // for it
+            const uint32_t fm = s->formats.load();
+            for (Slot& sl : s->slots) {
+                if (sl.busy || sl.graph_formats == fm) continue;
+                if (!build_graph(s, sl)) {
+                    fail(s, HTEX_ERR_CUDA);
+                    return;
+                }
+                progress = true;
+            }
+        }
+        if (!progress) {
             bool idle = s->waiting.empty() && s->admitted.empty();
             for (const Slot& sl : s->slots) idle = idle && !sl.busy;
             std::unique_lock<std::mutex> g(s->mu);

@@ -158,9 +158,10 @@ def source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-# the files the filter kernel is compiled from (and the build flags)
+# the files the filter kernel is compiled from (and the build flags), and lookup.cu, whose sort sets the
+# order (hence the DRAM traffic) of the queries it filters
 FILTER_SOURCES = ("csrc/lookup_kernels.cuh", "csrc/lookup_u8.cu", "csrc/lookup_core.cuh", "csrc/fetch.cuh",
-                  "csrc/htex_internal.h", "build.py")
+                  "csrc/htex_internal.h", "build.py", "csrc/lookup.cu")
 
 
 def filter_source_hash() -> str:
@@ -479,7 +480,7 @@ def main():
         sq = torch.empty_like(q)
         pos = torch.empty(nq, dtype=torch.int32, device="cuda")
         sout = torch.empty_like(out)
-    sort_chunk = 1 << 23
+    sort_chunk = 1 << 24
     launches_per_step = (2 * -(-nq // sort_chunk) + 2) if use_bin else 1
 
     def step(ev=None):
@@ -677,8 +678,9 @@ def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7, repeats:
 
     def run_server(cfg, budget, arrivals, sizes, tags):
         server = new_server(cfg, budget)
-        # warm-up: one small request per asset, served before the timed stream
-        serve.replay(server, np.zeros(len(assets)), np.full(len(assets), 1024), np.arange(len(assets)), qsrc,
+        # warm-up: one request per asset (large enough to wait for its asset's upload), served before the
+        # timed stream
+        serve.replay(server, np.zeros(len(assets)), np.full(len(assets), 131072), np.arange(len(assets)), qsrc,
                      lambda k, a, n: out_arena.data_ptr())
         lat, wall = serve.replay(server, arrivals, sizes, tags, qsrc, lambda k, a, n: out_arena.data_ptr())
         st = server.stats()

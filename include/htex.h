@@ -243,7 +243,7 @@ void htex_textures_destroy(htex_textures* t);
  *   out       device [n][channels] float (16-byte aligned when channels = 4)
  *   flags     HTEX_LOOKUP_BIN: when the pool exceeds 64 MiB, counting-sort
  *             the queries into ranges of consecutive halfedges first, in
- *             chunks of 2^23 queries, filter them in that order and gather
+ *             chunks of 2^24 queries, filter them in that order and gather
  *             the results back into query order (same results, bit for bit;
  *             scratch of 20 + 4 * channels bytes per chunk query,
  *             allocated stream-ordered on 'stream' from a library-owned
@@ -297,7 +297,7 @@ htex_status htex_lookup_aniso(const htex_textures* t, const htex_query_aniso* q,
  * own, Section 4.4, Alg. 3), only which texels share L2 at a time.
  *
  * htex_queries_sort: counting-sorts the queries, within consecutive chunks
- * of 2^23, into ranges of consecutive halfedges (at most 128 ranges of
+ * of 2^24, into ranges of consecutive halfedges (at most 128 ranges of
  * 2^s halfedges, the ranges in ascending order, invalid queries last in
  * their chunk; the order inside a range is unspecified and may differ
  * from call to call).
@@ -353,7 +353,7 @@ htex_status htex_lookup_host(const htex_textures* t, const htex_query* q, int64_
  *                size), same element order as the pool; accumulated into
  *                (the caller zeroes it); padding elements stay untouched
  *   flags        HTEX_LOOKUP_BIN: when the pool exceeds 64 MiB, sort the
- *                queries as htex_lookup does (chunks of 2^23, ranges of
+ *                queries as htex_lookup does (chunks of 2^24, ranges of
  *                consecutive halfedges; grad_out rows move with their
  *                queries) so that the threads resident together add into
  *                a narrow range of textures; lanes of a warp whose taps
@@ -450,10 +450,14 @@ htex_status htex_displace(const htex_geometry* g, const htex_textures* t, int32_
  * batching.  The paper renders one asset per frame; this serves the same
  * per-query computation (Alg. 3) to a stream of requests.  A scheduler
  * thread owned by the server
- *   - uploads an asset when a request needs it and it fits the budget,
- *     evicting the least recently used assets that no admitted request
- *     still needs; requests whose asset does not fit yet wait (later
- *     requests whose asset fits go ahead);
+ *   - admits a request when its asset is resident, and a small request
+ *     (at most 65,536 queries) at once: while its asset is not resident
+ *     (or still uploading) its batches read the asset's page-locked host
+ *     copy across the CPU-GPU link (same kernel, same bytes, so the same
+ *     results); larger requests wait for the upload;
+ *   - uploads the assets that unfinished requests need, most requested
+ *     first, as far as the budget allows after evicting the least recently
+ *     used assets that no unfinished request needs;
  *   - fills each free batch slot from the admitted requests, shortest
  *     remaining work first with ageing (the remaining query count is
  *     divided by 1 + wait / 1 ms, so small requests overtake large ones
@@ -484,6 +488,7 @@ typedef struct {
     int64_t uploads;         /* asset uploads (admissions)          */
     int64_t evictions;       /* assets evicted to make room         */
     int64_t resident_bytes;  /* device bytes of resident assets now */
+    int64_t host_queries;    /* queries served from an asset's host copy */
 } htex_server_stats;
 
 /* Create a server on the current device (allocates its staging, streams
@@ -493,7 +498,9 @@ htex_status htex_server_create(const htex_server_config* cfg, htex_server** out)
 /* Register an asset from a prepared pool (htex_textures_prepare layout;
  * scales required for scaled formats).  The pool is copied into page-locked
  * host memory owned by the server; the asset becomes resident on demand.
- * HTEX_ERR_OUT_OF_MEMORY if it alone exceeds the budget. */
+ * HTEX_ERR_OUT_OF_MEMORY if it alone exceeds the budget.  The host copy
+ * (records, headers, scales and pool) is page-locked and mapped, so
+ * requests can be served from it before the asset is resident. */
 htex_status htex_server_add_asset(htex_server* s, const htex_mesh* m, int32_t channels, htex_dtype dtype,
                                   const int32_t* log2_res, const void* pool, const float* scales,
                                   int32_t* asset_id);

@@ -17,7 +17,7 @@
 //
 // Binning (HTEX_LOOKUP_BIN), for pools well beyond L2: the queries are
 // counting-sorted into 128 ranges of consecutive halfedges, in chunks of
-// 2^23 queries, before filtering.  The filter kernel then works through
+// 2^24 queries, before filtering.  The filter kernel then works through
 // one range of the asset at a time, so that a texel sector fetched for one
 // query is still in L2 when the queries next to it in the range need it;
 // the ranges' order matters, the order inside a range does not.  The
@@ -272,30 +272,52 @@ __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const int4* q, i
 }
 
 // Results back in query order: out[i] = sorted_out[pos[i]] (NaN where
-// pos[i] is not in [0, m)).
+// pos[i] is not in [0, m)).  Each thread has kGatherRows rows in flight:
+// all their positions, then all their loads, then all their stores (a
+// store between two loads would keep the second load from being issued
+// early, since the compiler cannot prove the rows do not overlap).
+constexpr int kGatherRows = 8;
+
 template <int C>
-__global__ void k_chunk_gather(const float* sout, const int32_t* pos, int64_t m, float* out) {
+__global__ void k_chunk_gather(const float* __restrict__ sout, const int32_t* __restrict__ pos, int64_t m,
+                               float* __restrict__ out) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < m; i0 += 4 * stride) {
-        int64_t p[4];
+    for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < m; i0 += kGatherRows * stride) {
+        int64_t p[kGatherRows];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) p[k] = i0 + k * stride < m ? int64_t(__ldcs(pos + i0 + k * stride)) : 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < kGatherRows; ++k) {
             const int64_t i = i0 + k * stride;
-            if (i >= m) continue;
-            if (uint64_t(p[k]) >= uint64_t(m)) {   // not a position of this batch: NaN, no read
+            p[k] = i < m ? int64_t(__ldcs(pos + i)) : -1;
+        }
+        float v[kGatherRows][C];
 #pragma unroll
-                for (int c = 0; c < C; ++c) out[i * C + c] = __int_as_float(0x7fc00000);
-                continue;
-            }
+        for (int k = 0; k < kGatherRows; ++k) {
+            const bool ok = uint64_t(p[k]) < uint64_t(m);   // else not a position of this batch: NaN, no read
             if constexpr (C == 4) {
-                __stcs(reinterpret_cast<float4*>(out) + i, __ldcg(reinterpret_cast<const float4*>(sout) + p[k]));
+                const float4 r = ok ? __ldcg(reinterpret_cast<const float4*>(sout) + p[k])
+                                    : make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                                                  __int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+                v[k][0] = r.x; v[k][1] = r.y; v[k][2] = r.z; v[k][3] = r.w;
             } else if constexpr (C == 2) {
-                __stcs(reinterpret_cast<float2*>(out) + i, __ldcg(reinterpret_cast<const float2*>(sout) + p[k]));
+                const float2 r = ok ? __ldcg(reinterpret_cast<const float2*>(sout) + p[k])
+                                    : make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+                v[k][0] = r.x; v[k][1] = r.y;
             } else {
 #pragma unroll
-                for (int c = 0; c < C; ++c) __stcs(out + i * C + c, __ldcg(sout + p[k] * C + c));
+                for (int c = 0; c < C; ++c) v[k][c] = ok ? __ldcg(sout + p[k] * C + c) : __int_as_float(0x7fc00000);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kGatherRows; ++k) {
+            const int64_t i = i0 + k * stride;
+            if (i >= m) break;
+            if constexpr (C == 4) {
+                __stcs(reinterpret_cast<float4*>(out) + i, make_float4(v[k][0], v[k][1], v[k][2], v[k][3]));
+            } else if constexpr (C == 2) {
+                __stcs(reinterpret_cast<float2*>(out) + i, make_float2(v[k][0], v[k][1]));
+            } else {
+#pragma unroll
+                for (int c = 0; c < C; ++c) __stcs(out + i * C + c, v[k][c]);
             }
         }
     }
@@ -308,7 +330,7 @@ using namespace htex;
 namespace {
 
 #ifndef HTEX_SORT_CHUNK_LOG2
-#define HTEX_SORT_CHUNK_LOG2 23
+#define HTEX_SORT_CHUNK_LOG2 24
 #endif
 #ifndef HTEX_CHUNK_BUCKETS
 #define HTEX_CHUNK_BUCKETS 128

@@ -5,9 +5,13 @@
 // A scheduler thread owns the device side.  Each pass it
 //   1. retires finished batches (event query) and records the completion
 //      time of every request whose last queries were in them;
-//   2. admits waiting requests: their asset is uploaded (asynchronously,
-//      from page-locked host memory) once it fits the budget, evicting the
-//      least recently used assets that no admitted request still needs;
+//   2. admits requests whose asset is resident, and small requests at
+//      once: until their asset is resident their batches read the asset's
+//      page-locked, mapped host copy across the CPU-GPU link; assets that
+//      unfinished requests need are uploaded (asynchronously, from that
+//      host copy), most requested first, as far as the budget allows after
+//      evicting the least recently used assets that no unfinished request
+//      needs;
 //   3. fills every free batch slot from the admitted requests, shortest
 //      remaining work first with ageing (a request's remaining query count
 //      shrinks with the time it has waited, so small requests overtake
@@ -150,7 +154,12 @@ struct Request {
 
 struct ServeAsset {
     HtexAssetArrays arrays;
-    void* pinned_pool = nullptr;
+    // page-locked, mapped host copy: records, headers, scales, pool (each
+    // 256-byte aligned); the device addresses of its parts serve requests
+    // while the asset is not resident, the host addresses feed uploads
+    void* host = nullptr;
+    size_t off_hdr = 0, off_scale = 0, off_pool = 0;
+    const uint8_t* dev_host = nullptr;
     int64_t bytes = 0;
     int fmt = 0;
     htex_textures* tex = nullptr;   // resident when set
@@ -290,11 +299,35 @@ bool make_room(htex_server* s, int64_t need) {
     return true;
 }
 
+// The four parts of an asset's host copy to its device buffers.
+htex_status copy_host_copy(const ServeAsset* a, htex_textures* t, cudaStream_t stream) {
+    const uint8_t* h = static_cast<const uint8_t*>(a->host);
+    const size_t rec_b = a->arrays.rec.size() * 4, hdr_b = a->arrays.hdr.size() * 4, sc_b = a->arrays.scale.size() * 4;
+    if ((rec_b && cudaMemcpyAsync(t->d_rec, h, rec_b, cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
+        (hdr_b && cudaMemcpyAsync(t->d_hdr, h + a->off_hdr, hdr_b, cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
+        (sc_b && cudaMemcpyAsync(t->d_scale, h + a->off_scale, sc_b, cudaMemcpyHostToDevice, stream) != cudaSuccess) ||
+        (a->arrays.pool_bytes && cudaMemcpyAsync(t->d_pool, h + a->off_pool, size_t(a->arrays.pool_bytes),
+                                                 cudaMemcpyHostToDevice, stream) != cudaSuccess)) {
+        cudaGetLastError();
+        return HTEX_ERR_CUDA;
+    }
+    return HTEX_OK;
+}
+
+// A request is admitted when its asset is resident.  A small request
+// (at most kHostServeQueries) whose asset is not resident, or still
+// uploading, is admitted at once: its batches read the asset's page-locked
+// host copy across the CPU-GPU link, with the same kernel code and bytes.
+// (Texel reads across the link cost several times the bytes of the query
+// and result, so large requests wait for the upload instead.)  Assets with
+// unfinished requests are uploaded, most requested first, as far as the
+// budget allows after evicting idle assets.
+constexpr int64_t kHostServeQueries = 65536;
+
 bool admit(htex_server* s) {
     bool progress = false;
-    // finished uploads make their waiting requests admissible
     const int32_t na = s->num_assets.load();
-    for (int32_t k = 0; k < na; ++k) {
+    for (int32_t k = 0; k < na; ++k) {      // finished uploads
         ServeAsset* a = s->assets[k];
         if (!a->uploading) continue;
         const cudaError_t e = cudaEventQuery(a->uploaded);
@@ -309,30 +342,37 @@ bool admit(htex_server* s) {
     for (size_t k = 0; k < s->waiting.size();) {
         Request* r = s->waiting[k];
         ServeAsset* a = s->assets[r->asset];
-        if (!a->tex) {
-            if (!make_room(s, a->bytes)) { ++k; continue; }
-            htex_textures* t = nullptr;
-            if (htex_asset_allocate_async(a->arrays, s->asset_pool, s->upload_stream, &t) != HTEX_OK) { ++k; continue; }
-            if (htex_asset_copy_async(a->arrays, a->pinned_pool, t, s->upload_stream) != HTEX_OK ||
-                cudaEventRecord(a->uploaded, s->upload_stream) != cudaSuccess) {
-                htex_textures_destroy(t);
-                fail(s, HTEX_ERR_CUDA);
-                return false;
-            }
-            a->tex = t;
-            a->uploading = true;
-            s->resident_bytes += a->bytes;
-            {
-                std::lock_guard<std::mutex> g(s->mu);
-                ++s->stats.uploads;
-            }
-            progress = true;
+        if (!(a->tex && !a->uploading) && r->n > kHostServeQueries) {
+            ++k;
+            continue;
         }
-        if (a->uploading) { ++k; continue; }
-        a->last_use = ++s->tick;
         r->active = true;
+        a->last_use = ++s->tick;
         s->admitted.push_back(r);
         s->waiting.erase(s->waiting.begin() + long(k));
+        progress = true;
+    }
+    std::vector<ServeAsset*> want;
+    for (int32_t k = 0; k < na; ++k)
+        if (!s->assets[k]->tex && s->assets[k]->pins > 0) want.push_back(s->assets[k]);
+    std::stable_sort(want.begin(), want.end(), [](const ServeAsset* x, const ServeAsset* y) { return x->pins > y->pins; });
+    for (ServeAsset* a : want) {
+        if (!make_room(s, a->bytes)) continue;
+        htex_textures* t = nullptr;
+        if (htex_asset_allocate_async(a->arrays, s->asset_pool, s->upload_stream, &t) != HTEX_OK) continue;
+        if (copy_host_copy(a, t, s->upload_stream) != HTEX_OK ||
+            cudaEventRecord(a->uploaded, s->upload_stream) != cudaSuccess) {
+            htex_textures_destroy(t);
+            fail(s, HTEX_ERR_CUDA);
+            return false;
+        }
+        a->tex = t;
+        a->uploading = true;
+        s->resident_bytes += a->bytes;
+        {
+            std::lock_guard<std::mutex> g(s->mu);
+            ++s->stats.uploads;
+        }
         progress = true;
     }
     return progress;
@@ -382,6 +422,7 @@ bool launch_batch(htex_server* s, Slot& sl) {
         return s->assets[x.first->asset]->fmt < s->assets[y.first->asset]->fmt;
     });
     ServeTable* T = sl.h_table;
+    int64_t host_queries = 0;
     std::memset(T->counter, 0, sizeof(T->counter));
     std::memset(T->num_items, 0, sizeof(T->num_items));
     std::memset(T->total_tiles, 0, sizeof(T->total_tiles));
@@ -390,23 +431,25 @@ bool launch_batch(htex_server* s, Slot& sl) {
         Request* r = take[k].first;
         const int64_t c = take[k].second;
         ServeAsset* a = s->assets[r->asset];
-        const htex_textures* t = a->tex;
+        const htex_textures* t = (a->tex && !a->uploading) ? a->tex : nullptr;   // resident, else the host copy
+        const HtexAssetArrays& ar = a->arrays;
         const int f = a->fmt;
         if (T->num_items[f] == 0) T->first_item[f] = uint32_t(k);
         T->num_items[f] += 1;
         T->tile_start[k] = T->total_tiles[f];
         T->total_tiles[f] += uint32_t((c + kServeTile - 1) / kServeTile);
         ItemDesc& d = T->items[k];
-        d.rec = static_cast<const uint8_t*>(t->d_rec);
-        d.hdr = static_cast<const uint8_t*>(t->d_hdr);
-        d.scale = static_cast<const uint8_t*>(t->d_scale);
-        d.pool = static_cast<const uint8_t*>(t->d_pool);
+        d.rec = t ? static_cast<const uint8_t*>(t->d_rec) : a->dev_host;
+        d.hdr = t ? static_cast<const uint8_t*>(t->d_hdr) : a->dev_host + a->off_hdr;
+        d.scale = t ? static_cast<const uint8_t*>(t->d_scale) : a->dev_host + a->off_scale;
+        d.pool = t ? static_cast<const uint8_t*>(t->d_pool) : a->dev_host + a->off_pool;
         d.q = r->dq ? r->dq + r->issued : sl.d_q + qoff;
-        d.out = r->dout ? r->dout + r->issued * t->C : sl.d_out + ooff;
-        d.H = t->H;
-        d.uniform_log2n = t->uniform_log2n;
-        d.uniform_stride16 = uint32_t(t->uniform_stride / 16);
+        d.out = r->dout ? r->dout + r->issued * ar.C : sl.d_out + ooff;
+        d.H = ar.H;
+        d.uniform_log2n = ar.uniform_log2n;
+        d.uniform_stride16 = uint32_t(ar.uniform_stride / 16);
         d.n = int32_t(c);
+        if (!t) host_queries += c;
         if (!r->dq) {
             if (cudaMemcpyAsync(sl.d_q + qoff, r->q + r->issued, size_t(c) * sizeof(htex_query),
                                 cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) {
@@ -415,7 +458,7 @@ bool launch_batch(htex_server* s, Slot& sl) {
             }
             qoff += c;
         }
-        if (!r->dout) ooff += c * t->C;
+        if (!r->dout) ooff += c * ar.C;
         a->last_use = ++s->tick;
     }
     if (cudaGraphLaunch(sl.exec, sl.stream) != cudaSuccess) {
@@ -426,7 +469,7 @@ bool launch_batch(htex_server* s, Slot& sl) {
     for (size_t k = 0; k < take.size(); ++k) {
         Request* r = take[k].first;
         const int64_t c = take[k].second;
-        const int C = s->assets[r->asset]->tex->C;
+        const int C = s->assets[r->asset]->arrays.C;
         if (!r->dout) {
             if (cudaMemcpyAsync(r->out + r->issued * C, sl.d_out + ooff, size_t(c) * C * sizeof(float),
                                 cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess) {
@@ -446,6 +489,7 @@ bool launch_batch(htex_server* s, Slot& sl) {
         std::lock_guard<std::mutex> g(s->mu);
         ++s->stats.batches;
         s->stats.queries += used;
+        s->stats.host_queries += host_queries;
     }
     sl.busy = true;
     // requests with everything issued leave the admitted list (their
@@ -517,7 +561,7 @@ void release(htex_server* s) {
         ServeAsset* a = s->assets[k];
         htex_textures_destroy(a->tex);
         if (a->uploaded) cudaEventDestroy(a->uploaded);
-        cudaFreeHost(a->pinned_pool);
+        cudaFreeHost(a->host);
         delete a;
     }
     if (s->upload_stream) {
@@ -613,25 +657,38 @@ extern "C" htex_status htex_server_add_asset(htex_server* s, const htex_mesh* m,
         delete a;
         return HTEX_ERR_OUT_OF_MEMORY;
     }
-    if (cudaHostAlloc(&a->pinned_pool, size_t(std::max<int64_t>(a->arrays.pool_bytes, 16)), cudaHostAllocDefault) != cudaSuccess ||
+    const auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t rec_b = a->arrays.rec.size() * 4, hdr_b = a->arrays.hdr.size() * 4, sc_b = a->arrays.scale.size() * 4;
+    a->off_hdr = up(rec_b);
+    a->off_scale = a->off_hdr + up(hdr_b);
+    a->off_pool = a->off_scale + up(sc_b);
+    const size_t total = a->off_pool + up(size_t(std::max<int64_t>(a->arrays.pool_bytes, 16)));
+    void* dev = nullptr;
+    if (cudaHostAlloc(&a->host, total, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(&dev, a->host, 0) != cudaSuccess ||
         cudaEventCreateWithFlags(&a->uploaded, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        cudaFreeHost(a->pinned_pool);
+        cudaFreeHost(a->host);
         delete a;
         return HTEX_ERR_OUT_OF_MEMORY;
     }
-    std::memcpy(a->pinned_pool, pool, size_t(a->arrays.pool_bytes));
+    a->dev_host = static_cast<const uint8_t*>(dev);
+    uint8_t* h = static_cast<uint8_t*>(a->host);
+    std::memcpy(h, a->arrays.rec.data(), rec_b);
+    std::memcpy(h + a->off_hdr, a->arrays.hdr.data(), hdr_b);
+    std::memcpy(h + a->off_scale, a->arrays.scale.data(), sc_b);
+    std::memcpy(h + a->off_pool, pool, size_t(a->arrays.pool_bytes));
     std::lock_guard<std::mutex> g(s->mu);
     if (s->error != HTEX_OK) {
         cudaEventDestroy(a->uploaded);
-        cudaFreeHost(a->pinned_pool);
+        cudaFreeHost(a->host);
         delete a;
         return s->error;
     }
     const int32_t k = s->num_assets.load();
     if (k >= kMaxAssets) {
         cudaEventDestroy(a->uploaded);
-        cudaFreeHost(a->pinned_pool);
+        cudaFreeHost(a->host);
         delete a;
         return HTEX_ERR_UNSUPPORTED;
     }

@@ -23,7 +23,8 @@ class Config(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("queries", ctypes.c_int64), ("batches", ctypes.c_int64),
-                ("uploads", ctypes.c_int64), ("evictions", ctypes.c_int64), ("resident_bytes", ctypes.c_int64)]
+                ("uploads", ctypes.c_int64), ("evictions", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
+                ("host_queries", ctypes.c_int64)]
 
 
 class Server:

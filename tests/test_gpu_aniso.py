@@ -133,13 +133,13 @@ def test_aniso_invalid_queries_and_arguments():
 
 def test_sorted_aniso_equals_unsorted_multi_chunk():
     """HTEX_LOOKUP_BIN on the anisotropic lookup: 32-byte queries sorted by
-    halfedge range in chunks of 2^23 (a full chunk and a ragged one, invalid
+    halfedge range in chunks of 2^24 (a full chunk and a ragged one, invalid
     queries inside) on a pool above the 64 MiB threshold give the unsorted
     results bit for bit, and the oracle's on a sample."""
     gen = lambda: syn.cylinder(around=128, rows=60, seed=14)
     mo, to, tl = _case(gen, lambda E: np.full(E, 5, np.int32), 4, "u8", hx.BUILD_MIPS, seed=15)
     assert tl.pool_bytes > (64 << 20)
-    n = (1 << 23) + 1237
+    n = (1 << 24) + 1237
     qs = tuple(np.array(x) for x in _aniso_queries(mo.H, n, seed=16, lo=-8, hi=0))
     qs[0][::70001] = -2
     q = torch.from_numpy(hx.pack_queries_aniso(*qs)).cuda()

@@ -84,7 +84,7 @@ def test_fit_to_smooth_target():
 
 def test_sorted_backward_matches_unsorted_and_oracle():
     """HTEX_LOOKUP_BIN on the adjoint: queries sorted by halfedge range in
-    chunks of 2^23 with their upstream gradients following them (a full
+    chunks of 2^24 with their upstream gradients following them (a full
     chunk plus a ragged one, invalid queries inside), on a pool above the
     64 MiB threshold.  The gradient equals the unsorted kernel's and the
     oracle's up to float-atomic reordering (1e-5 relative to the largest
@@ -96,7 +96,7 @@ def test_sorted_backward_matches_unsorted_and_oracle():
     tex_np = syn.texels_f32(log2n, 1, seed=15)
     tex = hx.Textures.upload(mesh, log2n, tex_np, 1, "f32", hx.BUILD_MIPS)
     assert tex.pool_bytes > (64 << 20)
-    n = (1 << 23) + 4099
+    n = (1 << 24) + 4099
     h, u, v, f = syn.queries(mesh.H, n, seed=16, footprint="loguniform", lo=-7, hi=0.5)
     h[::50021] = -1
     q = torch.from_numpy(hx.pack_queries(h, u, v, f)).cuda()

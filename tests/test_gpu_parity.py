@@ -259,7 +259,7 @@ def test_binned_lookup_mid_asset():
 
 @pytest.mark.parametrize("fmt,C,n", [("u8", 4, 32), ("f32", 3, 16), ("f16", 1, 64), ("bf16", 2, 32)])
 def test_sorted_lookup_multi_chunk(fmt, C, n):
-    """The sorted path works on chunks of 2^23 queries: a full chunk plus a
+    """The sorted path works on chunks of 2^24 queries: a full chunk plus a
     ragged one, every channel count (results go back to their queries'
     places), equal bit for bit to the unsorted kernel and to the oracle
     within 1e-5 on a sample (invalid queries included)."""
@@ -267,7 +267,7 @@ def test_sorted_lookup_multi_chunk(fmt, C, n):
     log2n_fn = _u(int(np.log2(n)))
     mo, to, tl, *_ = _case(gen, log2n_fn, C, fmt, hx.BUILD_MIPS | hx.MIRROR_BOUNDARY, seed=17)
     assert tl.pool_bytes > (64 << 20)
-    h, u, v, f = syn.queries(mo.H, (3 << 22) + 4321, seed=18, footprint="loguniform")
+    h, u, v, f = syn.queries(mo.H, (3 << 23) + 4321, seed=18, footprint="loguniform")
     hb, ub, vb, fb = syn.invalid_queries(mo.H)
     k = len(h) // 2
     qs = tuple(np.concatenate([a[:k], b, a[k:]]) for a, b in zip((h, u, v, f), (hb, ub, vb, fb)))
@@ -289,13 +289,13 @@ def _range_shift(H, ranges=128):
 
 def test_sort_queries_and_gather_results():
     """htex_queries_sort permutes the queries (each one unchanged, pos its
-    new place) into ascending halfedge ranges within each 2^23-query chunk,
+    new place) into ascending halfedge ranges within each 2^24-query chunk,
     invalid queries last; filtering the sorted copy and gathering the
     results back equals the unsorted lookup bit for bit; a gather position
     outside [0, n) gives NaN."""
     gen = lambda: syn.cylinder(around=128, rows=60, seed=14)
     mo, to, tl, *_ = _case(gen, _u(5), 4, "u8", hx.BUILD_MIPS | hx.MIRROR_BOUNDARY, seed=15)
-    n = (1 << 23) + 77777
+    n = (1 << 24) + 77777
     h, u, v, f = syn.queries(mo.H, n, seed=19, footprint="loguniform")
     h[::1001] = -3
     h[5::2003] = mo.H
@@ -308,10 +308,10 @@ def test_sort_queries_and_gather_results():
     s = _range_shift(mo.H)
     hs = sq_np[:, 0].astype(np.int64)
     key = np.where((hs >= 0) & (hs < mo.H), hs >> s, 1 << 40)
-    for c0 in range(0, n, 1 << 23):
-        k = key[c0:c0 + (1 << 23)]
+    for c0 in range(0, n, 1 << 24):
+        k = key[c0:c0 + (1 << 24)]
         assert np.all(np.diff(k) >= 0)
-        assert np.all((p[c0:c0 + (1 << 23)] >= c0) & (p[c0:c0 + (1 << 23)] < c0 + len(k)))
+        assert np.all((p[c0:c0 + (1 << 24)] >= c0) & (p[c0:c0 + (1 << 24)] < c0 + len(k)))
     sout = hx.lookup(tl, sq)
     got = hx.gather_results(sout, pos)
     ref = hx.lookup(tl, q)

@@ -1,7 +1,8 @@
 """GPU tests of the lookup server (htex_server_*): every request's results
 are the same alone and in the mix, while the device budget forces assets
-to be evicted and uploaded again, for requests served in place from pinned
-buffers and for requests staged through device copies."""
+to be evicted and uploaded again (requests for an asset that is not
+resident read its host copy meanwhile), for requests served in place from
+pinned buffers and for requests staged through device copies."""
 import numpy as np
 import pytest
 
@@ -71,6 +72,7 @@ def test_server_results_equal_standalone_lookups():
     assert st["completed"] == len(reqs) + 1
     assert st["evictions"] > 0 and st["uploads"] > len(assets)
     assert st["resident_bytes"] <= budget
+    assert 0 < st["host_queries"] < st["queries"]   # some batches read a non-resident asset's host copy
     with pytest.raises(hx.HtexError):
         server.submit(17, 0, 1, 0)
     server.close()

@@ -548,7 +548,8 @@ def main():
                "h2d_bytes_per_step": int(q_host.numel() * 4), "d2h_bytes_per_step": int(out_host.numel() * 4),
                "steps": ksteps, "path": "htex_lookup_host on pinned host buffers: the lookup kernel reads the "
                                         "queries from and writes the results to host memory across the link, "
-                                        "queries in their given order"}
+                                        "queries in their given order",
+               "link": link_roofline(torch, q_host, out_host, q, out, ems / ksteps)}
 
     # the spec streaming case: the closed cube, 16x16 RGBA FP32, 2^24 queries
     cube = None if args.no_cube else cube_stream(hx, torch, stream, args)
@@ -609,6 +610,42 @@ def main():
 
 
 SERVER_CONFIG = {"batch_queries": 1 << 22, "batch_slots": 3, "max_items": 256, "request_chunk": 1 << 20}
+
+
+def link_roofline(torch, q_host, out_host, q_dev, out_dev, step_ms):
+    """The CPU-GPU link as the end-to-end bound: the same bytes the step
+    moves (queries in, results out) copied by the copy engines alone,
+    host-to-device and device-to-host concurrently on two streams, from
+    and to the same pinned buffers; 'frac' = that copy time over the step
+    time."""
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def both():
+        with torch.cuda.stream(s1):
+            q_dev.copy_(q_host, non_blocking=True)
+        with torch.cuda.stream(s2):
+            out_host.copy_(out_dev, non_blocking=True)
+
+    for _ in range(2):
+        both()
+    torch.cuda.synchronize()
+    reps = 5
+    cur = torch.cuda.current_stream()
+    ev[0].record(cur)
+    for _ in range(reps):
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        both()
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+    ev[1].record(cur)
+    torch.cuda.synchronize()
+    copy_ms = ev[0].elapsed_time(ev[1]) / reps
+    nbytes = q_host.numel() * 4 + out_host.numel() * 4
+    return {"bound": "cpu-gpu link", "bytes_per_step": int(nbytes), "copy_ms": copy_ms,
+            "copy_gbs": nbytes / (copy_ms / 1e3) / 1e9, "achieved_gbs": nbytes / (step_ms / 1e3) / 1e9,
+            "frac": copy_ms / step_ms}
 
 
 def serving_bench(hx, torch, n_requests: int = 2000, load: float = 0.7, repeats: int = 3, server_configs=None):

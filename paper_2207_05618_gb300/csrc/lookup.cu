@@ -137,9 +137,9 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const htex_query* q
 // result back in query order through the recorded positions.
 
 constexpr int kSortThreads = 256;
-constexpr int kSortPer = 8;
+constexpr int kSortPer = 8;   // 16-byte query words per thread and tile (16: 8% slower sort, measured)
 constexpr int kSortTile = kSortThreads * kSortPer;
-constexpr int kSortMaxBuckets = 256;   // keeps the scatter's static shared memory under 48 KiB
+constexpr int kSortMaxBuckets = 256;
 
 // QW: 16-byte words per query (1: htex_query, 2: htex_query_aniso); the
 // halfedge id is the first word's first int.
@@ -194,20 +194,37 @@ __device__ __forceinline__ void block_scan_buckets(const uint32_t* x, uint32_t* 
 
 // PC: floats of payload per query (rows of 'pay' in query order, moved to
 // 'spay' in sorted order with their queries); pos nullable.
+// Shared memory of k_chunk_scatter<QW, PC> (dynamic: a tile can exceed the
+// 48 KiB of static shared memory): the tile's queries (QW words each) and
+// payload rows, their buckets, and per bucket the first sorted position,
+// the tile's count, local offset and global base.
+template <int QW, int PC>
+struct ScatterSmem {
+    static constexpr int PER = kSortPer / QW / (PC > 0 ? 2 : 1), TILE = kSortThreads * PER;
+    static constexpr size_t tile = 0;
+    static constexpr size_t pay = tile + size_t(TILE) * QW * 16;
+    static constexpr size_t bucket = pay + ((size_t(PC > 0 ? TILE * PC : 1) * 4 + 15) & ~size_t(15));
+    static constexpr size_t arrays = bucket + ((size_t(TILE) * 2 + 15) & ~size_t(15));
+    static constexpr size_t warps = arrays + size_t(4) * kSortMaxBuckets * 4;
+    static constexpr size_t bytes = warps + (kSortThreads / 32) * 4;
+};
+
 template <int QW, int PC>
 __global__ void __launch_bounds__(kSortThreads) k_chunk_scatter(const int4* q, int64_t m, int32_t H, int shift,
                                                                 uint32_t B, const uint32_t* counts, uint32_t* taken,
                                                                 int4* sq, int32_t* pos, int32_t pos_base,
                                                                 const float* pay, float* spay) {
-    constexpr int PER = kSortPer / QW / (PC > 0 ? 2 : 1), TILE = kSortThreads * PER;
-    __shared__ int4 tile[TILE * QW];
-    __shared__ float tile_pay[PC > 0 ? TILE * PC : 1];
-    __shared__ uint16_t tile_bucket[TILE];
-    __shared__ uint32_t start[kSortMaxBuckets];    // first sorted position of each bucket
-    __shared__ uint32_t cnt[kSortMaxBuckets];      // the tile's bucket sizes
-    __shared__ uint32_t loff[kSortMaxBuckets];     // the tile's local bucket offsets
-    __shared__ uint32_t gbase[kSortMaxBuckets];    // where the tile's run of each bucket goes
-    __shared__ uint32_t warp_tot[kSortThreads / 32];
+    using L = ScatterSmem<QW, PC>;
+    constexpr int PER = L::PER, TILE = L::TILE;
+    extern __shared__ __align__(16) uint8_t smem[];
+    int4* tile = reinterpret_cast<int4*>(smem + L::tile);
+    float* tile_pay = reinterpret_cast<float*>(smem + L::pay);
+    uint16_t* tile_bucket = reinterpret_cast<uint16_t*>(smem + L::bucket);
+    uint32_t* start = reinterpret_cast<uint32_t*>(smem + L::arrays);   // first sorted position of each bucket
+    uint32_t* cnt = start + kSortMaxBuckets;                             // the tile's bucket sizes
+    uint32_t* loff = cnt + kSortMaxBuckets;                              // the tile's local bucket offsets
+    uint32_t* gbase = loff + kSortMaxBuckets;                            // where the tile's run of each bucket goes
+    uint32_t* warp_tot = reinterpret_cast<uint32_t*>(smem + L::warps);
     for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) cnt[b] = counts[b];
     __syncthreads();
     block_scan_buckets(cnt, start, B, warp_tot);
@@ -413,14 +430,18 @@ size_t counter_bytes(const SortPlan& P) { return (size_t(2 * P.B) * 4 + 255) & ~
 template <int QW, int PC = 0>
 htex_status launch_sort(const htex_textures* t, const SortPlan& P, const int4* q, int64_t m, uint32_t* counters,
                         int4* sq, int32_t* pos, cudaStream_t s, const float* pay = nullptr, float* spay = nullptr) {
-    constexpr int64_t TILE = int64_t(kSortThreads) * (kSortPer / QW / (PC > 0 ? 2 : 1));
-    const int64_t blocks = int64_t(t->num_sms) * resident_blocks(k_chunk_scatter<QW, PC>, kSortThreads, 0);
+    constexpr int64_t TILE = ScatterSmem<QW, PC>::TILE;
+    constexpr size_t smem = ScatterSmem<QW, PC>::bytes;
+    if (cudaFuncSetAttribute(k_chunk_scatter<QW, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+        cudaSuccess)
+        return HTEX_ERR_CUDA;
+    const int64_t blocks = int64_t(t->num_sms) * resident_blocks(k_chunk_scatter<QW, PC>, kSortThreads, smem);
     for (int64_t c0 = 0; c0 < m; c0 += kSortChunk) {
         const int64_t mc = std::min<int64_t>(kSortChunk, m - c0);
         const int64_t g = std::min<int64_t>((mc + TILE - 1) / TILE, blocks);
         if (cudaMemsetAsync(counters, 0, size_t(2 * P.B) * 4, s) != cudaSuccess) return HTEX_ERR_CUDA;
         k_chunk_count<QW><<<unsigned(g), kSortThreads, 0, s>>>(q + c0 * QW, mc, t->H, P.shift, P.B, counters);
-        k_chunk_scatter<QW, PC><<<unsigned(g), kSortThreads, 0, s>>>(
+        k_chunk_scatter<QW, PC><<<unsigned(g), kSortThreads, smem, s>>>(
             q + c0 * QW, mc, t->H, P.shift, P.B, counters, counters + P.B, sq + c0 * QW, pos ? pos + c0 : nullptr,
             int32_t(c0), PC ? pay + c0 * PC : nullptr, PC ? spay + c0 * PC : nullptr);
         if (cudaGetLastError() != cudaSuccess) return HTEX_ERR_CUDA;

@@ -114,6 +114,20 @@ __device__ __forceinline__ float dec1(uint32_t b) {
     else return __uint_as_float(b);
 }
 
+// Byte c of a packed word as a float, exactly: the byte placed in the low
+// mantissa bits of 2^23 (one byte permute) minus 2^23 (one add), instead of
+// an integer-to-float conversion on the slower conversion pipe.
+__device__ __forceinline__ float byte_as_float(uint32_t word, int c) {
+    return __uint_as_float(__byte_perm(word, 0x4B000000u, 0x7540u | uint32_t(c))) - 8388608.0f;
+}
+
+// Channel c of a packed 8-bit-per-channel texel word, decoded.
+template <int DT>
+__device__ __forceinline__ float dec_byte(uint32_t word, int c) {
+    if constexpr (DT == HTEX_U8) return byte_as_float(word, c);
+    else return dec1<DT>((word >> (8 * c)) & 0xffu);
+}
+
 // One texel: C decoded (unscaled) channels from byte offset o.
 template <int DT, int C, class S>
 __device__ __forceinline__ void load_texel(const S& s, typename S::off_t o, float (&t)[C]) {
@@ -138,7 +152,7 @@ __device__ __forceinline__ void load_texel(const S& s, typename S::off_t o, floa
                 t[0] = lo.x; t[1] = lo.y; t[2] = hi.x; t[3] = hi.y;
             } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) t[c] = dec1<DT>((r >> (8 * c)) & 0xffu);
+                for (int c = 0; c < 4; ++c) t[c] = dec_byte<DT>(r, c);
             }
         } else if constexpr (C == 2) {
             const uint32_t r = s.ld2(o);
@@ -186,7 +200,7 @@ __device__ __forceinline__ void load_texel_if(const S& s, bool p, typename S::of
                 t[0] = lo.x; t[1] = lo.y; t[2] = hi.x; t[3] = hi.y;
             } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) t[c] = dec1<DT>((r >> (8 * c)) & 0xffu);
+                for (int c = 0; c < 4; ++c) t[c] = dec_byte<DT>(r, c);
             }
         } else if constexpr (C == 2) {
             const uint32_t r = s.ld2_if(p, o);
@@ -251,7 +265,7 @@ struct Raw {
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < C; ++c) t[c] = dec1<DT>((a >> (8 * c)) & 0xffu);
+                for (int c = 0; c < C; ++c) t[c] = dec_byte<DT>(a, c);
             }
         } else {
             t[0] = dec1<DT>(a & 0xffffu);

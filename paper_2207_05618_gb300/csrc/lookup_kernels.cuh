@@ -79,7 +79,7 @@ __device__ __forceinline__ void lookup_loop_pairs(const Asset<S>& A, const FwdPa
 
 constexpr int kGlobalThreads = 256;
 #ifndef HTEX_GLOBAL_MIN_BLOCKS
-#define HTEX_GLOBAL_MIN_BLOCKS 3   // resident blocks per SM the register budget targets
+#define HTEX_GLOBAL_MIN_BLOCKS 2   // resident blocks per SM the register budget targets (3: 1.5% slower filter, measured)
 #endif
 constexpr int kStagedThreads = 384;
 

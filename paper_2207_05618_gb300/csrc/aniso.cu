@@ -115,7 +115,7 @@ template <int DT, int C>
 __device__ __forceinline__ void aniso_fetch(const Asset<GlobalSpace>& A, bool on, const FetchConst& f, float a,
                                             float b, float (&acc)[C], float& W) {
     const float x = f.flip ? 1.0f - a : a, y = f.flip ? 1.0f - b : b;
-    const float half = 0.5f / float(1 << f.n1);
+    const float half = __int_as_float((126 - f.n1) << 23);   // 2^-(n1 + 1): half a texel of the coarser level
     const bool near = on && x > -half && x < 1.0f + half && y > -half && y < 1.0f + half;
     if (!__any_sync(0xffffffffu, near)) return;
     aniso_level<DT, C>(A, f.base0, 1 << f.n0, x, y, near ? f.w0 : 0.0f, f.sc, acc, W);
@@ -143,6 +143,7 @@ struct AnisoQuery {
     float u, v, mu, mv;     // centre and the probe spacing axis (major axis times s)
     int32_t K;              // probes (0: the lane holds no query)
     int32_t ok;             // a valid query
+    float inv2K;            // 1 / (2K): probe k sits at t = (2k + 1 - K) / (2K)
     FetchConst f[3];        // own, Next, Prev
 };
 
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(kAnisoThreads) k_lookup_aniso(Asset<GlobalSpac
         Q.mu = (major_y ? dudy : dudx) * s;
         Q.mv = (major_y ? dvdy : dvdx) * s;
         Q.K = K;
+        Q.inv2K = 1.0f / float(2 * max(K, 1));
         Q.ok = ok;
         Q.f[0] = fetch_const<DT, C>(to, select_lod(lf, to.n), rec.x);
         Q.f[1] = fetch_const<DT, C>(tn, select_lod(lf, tn.n), rec.y);
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(kAnisoThreads) k_lookup_aniso(Asset<GlobalSpac
             const AnisoQuery& R = sq[wib][q];
             const bool on = has && R.ok;
             const int KR = R.K, k = j - qfirst;
-            const float t = (float(2 * k + 1) - float(KR)) / float(2 * KR);
+            const float t = float(2 * k + 1 - KR) * R.inv2K;
             const float pu = fmaf(R.mu, t, R.u), pv = fmaf(R.mv, t, R.v);
             float acc[C];
 #pragma unroll

@@ -138,14 +138,16 @@ constexpr int kAnisoWarps = kAnisoThreads / 32;
 constexpr int kAnisoMaxK = 16;
 
 // One query's constants, written by its lane, read by the lanes that run
-// its probes.
+// its probes.  120 bytes (30 words), so that lanes reading the same field
+// of different queries hit different shared-memory banks (a size of 32
+// words put them all in one bank).
 struct AnisoQuery {
     float u, v, mu, mv;     // centre and the probe spacing axis (major axis times s)
     int32_t K;              // probes (0: the lane holds no query)
-    int32_t ok;             // a valid query
-    float inv2K;            // 1 / (2K): probe k sits at t = (2k + 1 - K) / (2K)
+    float inv2K;            // +-1 / (2K), negative for an invalid query: probe k sits at t = (2k + 1 - K) / (2K)
     FetchConst f[3];        // own, Next, Prev
 };
+static_assert(sizeof(AnisoQuery) == 120, "AnisoQuery: 30 words (bank spread)");
 
 template <int DT, int C>
 __global__ void __launch_bounds__(kAnisoThreads) k_lookup_aniso(Asset<GlobalSpace> A, AnisoParams p) {
@@ -189,8 +191,7 @@ __global__ void __launch_bounds__(kAnisoThreads) k_lookup_aniso(Asset<GlobalSpac
         Q.mu = (major_y ? dudy : dudx) * s;
         Q.mv = (major_y ? dvdy : dvdx) * s;
         Q.K = K;
-        Q.inv2K = 1.0f / float(2 * max(K, 1));
-        Q.ok = ok;
+        Q.inv2K = (ok ? 1.0f : -1.0f) / float(2 * max(K, 1));
         Q.f[0] = fetch_const<DT, C>(to, select_lod(lf, to.n), rec.x);
         Q.f[1] = fetch_const<DT, C>(tn, select_lod(lf, tn.n), rec.y);
         Q.f[2] = fetch_const<DT, C>(tp, select_lod(lf, tp.n), rec.z);
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kAnisoThreads) k_lookup_aniso(Asset<GlobalSpac
             const int q = has ? owner[wib][j] : int(owner[wib][P - 1]);
             const int qfirst = __shfl_sync(0xffffffffu, first, q);
             const AnisoQuery& R = sq[wib][q];
-            const bool on = has && R.ok;
+            const bool on = has && R.inv2K > 0.0f;
             const int KR = R.K, k = j - qfirst;
             const float t = float(2 * k + 1 - KR) * R.inv2K;
             const float pu = fmaf(R.mu, t, R.u), pv = fmaf(R.mv, t, R.v);

@@ -988,7 +988,7 @@ def backward_bench(hx, torch, stream):
                   tex, qq, tt, grad_texels=grad, flags=hx.LOOKUP_BIN, stream=stream), 20),
               "adam_ms": timed(torch, stream, lambda: tex.adam_step(master, grad, m1, m2, 1, 0.0), 20)}
     # a short untimed fit first: the first step of the first fit in a process
-    # stalled the host for about 0.5 s (one-time loading, measured with
+    # stalled the host for about 0.5 s (a one-time cost, measured with
     # per-step events), which is not a cost of the step; every fit starts
     # from zero texels, so the timed fit is unaffected by it
     fit.fit(tex, lambda step: pre[step], steps=3, lr=0.05)

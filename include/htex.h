@@ -351,7 +351,7 @@ htex_status htex_lookup_host(const htex_textures* t, const htex_query* q, int64_
  *   grad_out     device [n][channels] float
  *   grad_texels  device float, one per pool element (pool_bytes / element
  *                size), same element order as the pool; accumulated into
- *                (the caller zeroes it); padding elements stay untouched
+ *                (the caller zeroes it); padding elements keep their values
  *   flags        HTEX_LOOKUP_BIN: when the pool exceeds 64 MiB, sort the
  *                queries as htex_lookup does (chunks of 2^24, ranges of
  *                consecutive halfedges; grad_out rows move with their
@@ -363,9 +363,12 @@ htex_status htex_lookup_host(const htex_textures* t, const htex_query* q, int64_
  *                bytes per chunk query from the library pool.
  *                HTEX_LOOKUP_GLOBAL ignored.
  *   d_status     as for htex_lookup
- * Uses float atomics (a float2 and a scalar one per three-channel texel
- * when grad_texels is 8-byte aligned): the summation order, hence the last
- * bits, may vary from run to run.  Asynchronous. */
+ * Uses float atomics; per three-channel texel, when grad_texels is 16-byte
+ * aligned, one four-float atomic if its three values share a 16-byte block
+ * (adding +0.0 to the block's fourth element, which keeps its value; -0.0
+ * there becomes +0.0), else a float2 and a scalar one (also when only
+ * 8-byte aligned), else three scalar ones.  The summation order, hence the
+ * last bits, may vary from run to run.  Asynchronous. */
 htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, int64_t n,
                                  const float* grad_out, float* grad_texels, uint32_t flags,
                                  htex_stream stream, int32_t* d_status);

@@ -103,6 +103,50 @@ __device__ __forceinline__ void red_texel(float* grad, uint64_t elem, const floa
     }
 }
 
+// Two horizontally adjacent texels (elements elem and elem + C), each added
+// when its flag is set.  Both set, with a 16-byte aligned gradient: three
+// channels take 2 atomics for half the pairs and 3 for the rest (the six
+// values cover 2 or 3 16-byte blocks; zeros pad the blocks' other
+// elements), against 3 on average texel by texel; two channels with elem a
+// multiple of 4 take one float4; one channel with elem even one float2.
+template <int C>
+__device__ __forceinline__ void red_pair(float* grad, uint64_t elem, const float* x, bool a0, bool a1, int vec) {
+    if (a0 && a1 && vec == 4) {
+        const uint32_t r = uint32_t(elem & 3u);
+        float* c = grad + (elem - r);
+        if constexpr (C == 3) {
+            const float* y = x + 3;
+            if (r == 0) {
+                atomicAdd(reinterpret_cast<float4*>(c), make_float4(x[0], x[1], x[2], y[0]));
+                atomicAdd(reinterpret_cast<float2*>(c + 4), make_float2(y[1], y[2]));
+            } else if (r == 1) {
+                atomicAdd(reinterpret_cast<float4*>(c), make_float4(0.0f, x[0], x[1], x[2]));
+                atomicAdd(reinterpret_cast<float4*>(c + 4), make_float4(y[0], y[1], y[2], 0.0f));
+            } else if (r == 2) {
+                atomicAdd(reinterpret_cast<float2*>(c + 2), make_float2(x[0], x[1]));
+                atomicAdd(reinterpret_cast<float4*>(c + 4), make_float4(x[2], y[0], y[1], y[2]));
+            } else {
+                atomicAdd(c + 3, x[0]);
+                atomicAdd(reinterpret_cast<float4*>(c + 4), make_float4(x[1], x[2], y[0], y[1]));
+                atomicAdd(c + 8, y[2]);
+            }
+            return;
+        } else if constexpr (C == 2) {
+            if (r == 0) {
+                atomicAdd(reinterpret_cast<float4*>(c), make_float4(x[0], x[1], x[2], x[3]));
+                return;
+            }
+        } else if constexpr (C == 1) {
+            if ((r & 1u) == 0) {
+                atomicAdd(reinterpret_cast<float2*>(grad + elem), make_float2(x[0], x[1]));
+                return;
+            }
+        }
+    }
+    if (a0) red_texel<C>(grad, elem, x, vec);
+    if (a1) red_texel<C>(grad, elem + C, x + C, vec);
+}
+
 // Sum of x over the lanes of the calling lane's group (peers: the lanes with
 // an equal key, from __match_any_sync); the group's lowest lane ends up
 // holding the total.  All 32 lanes call it together.  A tree over group
@@ -163,10 +207,11 @@ __device__ __forceinline__ void own_part(const BwdParams& p, const TexRef& t, ui
     if (!on) return;
     const int64_t b = int64_t(t.off / Fmt<DT>::ES + uint64_t(level_texels(t.n, l)) * C) +
                       (int64_t(ty.i) * N + tx.i) * C;
-    const int64_t o[4] = {0, C, int64_t(N) * C, int64_t(N + 1) * C};
+    bool act[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (inb[k] && (summed || w[k] != 0.0f)) red_texel<C>(p.grad, uint64_t(b + o[k]), v + k * C, p.vec);
+    for (int k = 0; k < 4; ++k) act[k] = inb[k] && (summed || w[k] != 0.0f);
+    red_pair<C>(p.grad, uint64_t(b), v, act[0], act[1], p.vec);                       // row j
+    red_pair<C>(p.grad, uint64_t(b + int64_t(N) * C), v + 2 * C, act[2], act[3], p.vec);   // row j + 1
 }
 
 // A Next (row) or Prev (column) fetch at level l: the two texels of row or
@@ -205,9 +250,13 @@ __device__ __forceinline__ void edge_part(const BwdParams& p, const TexRef& t, u
     const int64_t step = row ? 1 : N;
     const int64_t b = int64_t(t.off / Fmt<DT>::ES + uint64_t(level_texels(t.n, l)) * C) +
                       ((row ? int64_t(k) * N : int64_t(k)) + int64_t(ta.i) * step) * C;
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-        if (inb[q] && (summed || w[q] != 0.0f)) red_texel<C>(p.grad, uint64_t(b + q * step * C), v + q * C, p.vec);
+    const bool act0 = inb[0] && (summed || w[0] != 0.0f), act1 = inb[1] && (summed || w[1] != 0.0f);
+    if (row) {
+        red_pair<C>(p.grad, uint64_t(b), v, act0, act1, p.vec);
+    } else {
+        if (act0) red_texel<C>(p.grad, uint64_t(b), v, p.vec);
+        if (act1) red_texel<C>(p.grad, uint64_t(b + step * C), v + C, p.vec);
+    }
 }
 
 // One query's three fetches: their textures, level choices and coordinates.

@@ -381,7 +381,10 @@ htex_status htex_lookup_backward(const htex_textures* t, const htex_query* q, in
  * then the new value is written into the resident pool (the next lookup
  * sees it) and g is set to 0 (ready for the next accumulation).
  *   master, grad, m, v  device float [n], 16-byte aligned, n = pool_bytes
- *                       / 4 (pool element order, as htex_lookup_backward)
+ *                       / 4 (pool element order, as htex_lookup_backward);
+ *                       master nullable: NULL optimises the pool's own
+ *                       values in place (an FP32 pool holds them exactly;
+ *                       one read and one write of n floats fewer)
  *   step                >= 1; beta1, beta2 in [0, 1); eps > 0
  * HTEX_ERR_INVALID_ARG for other formats or sizes.  Asynchronous. */
 htex_status htex_textures_adam_step(htex_textures* t, float* master, float* grad, float* m, float* v, int64_t n,

@@ -185,13 +185,17 @@ class Textures:
                   stream=None) -> None:
         """htex_textures_adam_step: one Adam step on an FP32 asset's texels;
         updates master, m and v, writes the new values into the pool and
-        clears grad (all float32 CUDA tensors of pool_elements)."""
+        clears grad (all float32 CUDA tensors of pool_elements).  master
+        None: the pool's own values are optimised in place."""
         import torch
         for name, x in (("master", master), ("grad", grad), ("m", m), ("v", v)):
+            if x is None and name == "master":
+                continue
             if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
                     and x.numel() == self.pool_elements):
                 raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of pool_elements")
-        check(self._lib.htex_textures_adam_step(self._h, *[ctypes.c_void_p(x.data_ptr()) for x in (master, grad, m, v)],
+        ptrs = [ctypes.c_void_p(x.data_ptr() if x is not None else None) for x in (master, grad, m, v)]
+        check(self._lib.htex_textures_adam_step(self._h, *ptrs,
                                                 self.pool_elements, float(lr), float(betas[0]), float(betas[1]),
                                                 float(eps), int(step), _stream(stream)), "htex_textures_adam_step")
 

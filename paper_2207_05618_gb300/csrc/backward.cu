@@ -433,11 +433,11 @@ htex_status htex_launch_backward(const htex_textures* t, const htex_query* q, in
 //   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
 //   p = p - (lr / (1 - b1^t)) m / (sqrt(v) / sqrt(1 - b2^t) + eps).
 struct AdamParams {
-    float* master;
+    float* master;   // the values being optimised (the pool itself when no separate copy is kept)
     float* grad;
     float* m;
     float* v;
-    float* pool;
+    float* pool;     // null when master is the pool
     int64_t n;
     float b1, b2, eps, step_size, inv_sqrt_bc2;
 };
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
         reinterpret_cast<float4*>(a.master)[i] = p;
         reinterpret_cast<float4*>(a.m)[i] = m;
         reinterpret_cast<float4*>(a.v)[i] = v;
-        __stcs(reinterpret_cast<float4*>(a.pool) + i, p);
+        if (a.pool) __stcs(reinterpret_cast<float4*>(a.pool) + i, p);
         __stcs(reinterpret_cast<float4*>(a.grad) + i, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
     }
     for (int64_t i = 4 * n4 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n; i += stride) {
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
         a.master[i] = p;
         a.m[i] = m;
         a.v[i] = v;
-        a.pool[i] = p;
+        if (a.pool) a.pool[i] = p;
         a.grad[i] = 0.0f;
     }
 }
@@ -484,14 +484,19 @@ extern "C" htex_status htex_textures_adam_step(htex_textures* t, float* master, 
                                                int32_t step, htex_stream stream) {
     if (!t || t->dtype != HTEX_F32) return HTEX_ERR_INVALID_ARG;
     if (n != t->pool_bytes / 4 || step < 1) return HTEX_ERR_INVALID_ARG;
-    if (!master || !grad || !m || !v) return HTEX_ERR_INVALID_ARG;
+    if (!grad || !m || !v) return HTEX_ERR_INVALID_ARG;
+    float* pool = static_cast<float*>(t->d_pool);
+    if (!master) {   // the pool holds the values: one stream less, no copy to keep
+        master = pool;
+        pool = nullptr;
+    }
     const uintptr_t all = reinterpret_cast<uintptr_t>(master) | reinterpret_cast<uintptr_t>(grad) |
                           reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v);
     if ((all & 15u) != 0) return HTEX_ERR_INVALID_ARG;
     if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f)) return HTEX_ERR_INVALID_ARG;
     const double bc1 = 1.0 - std::pow(double(beta1), double(step));
     const double bc2 = 1.0 - std::pow(double(beta2), double(step));
-    const AdamParams a{master, grad, m, v, static_cast<float*>(t->d_pool), n, beta1, beta2, eps,
+    const AdamParams a{master, grad, m, v, pool, n, beta1, beta2, eps,
                        float(double(lr) / bc1), float(1.0 / std::sqrt(bc2))};
     const int64_t want = (n / 4 + 255) / 256 + 1;
     const unsigned grid = unsigned(std::min<int64_t>(want, int64_t(t->num_sms) * 8));

@@ -454,9 +454,10 @@ inline int4* words(htex_query* q) { return reinterpret_cast<int4*>(q); }
 
 // Gathers the results of a chunk back into query order.  Positions are
 // relative to the sorted chunk.
-htex_status launch_gather(const float* sout, const int32_t* pos, int64_t m, int C, float* out, int num_sms,
-                          cudaStream_t s) {
-    const unsigned g = unsigned(std::max(1, num_sms)) * 8;
+htex_status launch_gather(const float* sout, const int32_t* pos, int64_t m, int C, float* out, cudaStream_t s) {
+    // one block per 256 x kGatherRows rows (no grid-stride pass: the last
+    // wave balances better; 6% faster than 8 blocks per SM striding)
+    const unsigned g = unsigned(std::max<int64_t>(1, (m + 256 * kGatherRows - 1) / (256 * kGatherRows)));
     switch (C) {
     case 1: k_chunk_gather<1><<<g, 256, 0, s>>>(sout, pos, m, out); break;
     case 2: k_chunk_gather<2><<<g, 256, 0, s>>>(sout, pos, m, out); break;
@@ -465,16 +466,6 @@ htex_status launch_gather(const float* sout, const int32_t* pos, int64_t m, int 
     default: return HTEX_ERR_INVALID_ARG;
     }
     return cudaGetLastError() == cudaSuccess ? HTEX_OK : HTEX_ERR_CUDA;
-}
-
-int current_device_sms() {
-    static std::mutex mu;
-    static int sms[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-    std::lock_guard<std::mutex> g(mu);
-    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms[dev] = 0;
-    return sms[dev];
 }
 
 }  // namespace
@@ -512,7 +503,7 @@ htex_status htex_launch_lookup(const htex_textures* t, const htex_query* q, int6
         const int64_t m = std::min<int64_t>(M, n - c0);
         st = launch_sort<1>(t, P, words(q + c0), m, counters, words(sq), pos, s);
         if (st == HTEX_OK) st = launch_fwd_dt<false>(t, FwdParams{sq, m, sout, d_status, nullptr}, fwd_flags, s);
-        if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, t->num_sms, s);
+        if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, s);
     }
     cudaFreeAsync(scratch, s);
     return st;
@@ -592,7 +583,7 @@ htex_status htex_launch_aniso_sorted(const htex_textures* t, const htex_query_an
         st = launch_sort<2>(t, P, reinterpret_cast<const int4*>(q + c0), m, counters, reinterpret_cast<int4*>(sq),
                             pos, s);
         if (st == HTEX_OK) st = htex_launch_aniso(t, sq, m, kmax, sout, stream, d_status);
-        if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, t->num_sms, s);
+        if (st == HTEX_OK) st = launch_gather(sout, pos, m, t->C, out + c0 * t->C, s);
     }
     cudaFreeAsync(scratch, s);
     return st;
@@ -630,7 +621,7 @@ extern "C" htex_status htex_results_gather(const float* sorted_out, const int32_
     if (((reinterpret_cast<uintptr_t>(sorted_out) | reinterpret_cast<uintptr_t>(out)) & (align - 1)) != 0 ||
         (reinterpret_cast<uintptr_t>(pos) & 3u) != 0)
         return HTEX_ERR_INVALID_ARG;
-    return launch_gather(sorted_out, pos, n, channels, out, current_device_sms(), reinterpret_cast<cudaStream_t>(stream));
+    return launch_gather(sorted_out, pos, n, channels, out, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" htex_status htex_lookup(const htex_textures* t, const htex_query* q, int64_t n, float* out,

@@ -3,9 +3,10 @@
 The lookup is linear in the stored texels, so its gradient is exact and
 cheap: ``htex_lookup_backward`` scatters dL/dvalue times the blend weights
 into a pool-shaped texel gradient (queries sorted by halfedge range, so the
-scatter-adds stay in L2).  ``fit`` runs Adam on an FP32 master copy of the
-pool with ``htex_textures_adam_step``, which also writes the new values
-into the resident textures and clears the gradient in the same pass.  The
+scatter-adds stay in L2).  ``fit`` runs Adam on the FP32 pool's own values
+in place with ``htex_textures_adam_step`` (an FP32 pool holds them
+exactly, so no separate master copy is kept), which also clears the
+gradient in the same pass.  The
 lookups, their adjoint and the optimiser step all run in libhtex's kernels.
 """
 from __future__ import annotations
@@ -37,12 +38,12 @@ def fit(tex: Textures, batches, steps: int = 200, lr: float = 0.05, init=None) -
     import torch
     if tex.dtype != "f32":
         raise ValueError("fit needs an FP32 asset (the master copy is written as stored values)")
-    master = (init.clone() if init is not None else
-              torch.zeros(tex.pool_elements, dtype=torch.float32, device="cuda"))
-    grad = torch.zeros_like(master)
-    m = torch.zeros_like(master)
-    v = torch.zeros_like(master)
-    tex.write_pool(master)
+    start = (init if init is not None else
+             torch.zeros(tex.pool_elements, dtype=torch.float32, device="cuda"))
+    tex.write_pool(start)
+    grad = torch.zeros(tex.pool_elements, dtype=torch.float32, device="cuda")
+    m = torch.zeros_like(grad)
+    v = torch.zeros_like(grad)
     res = FitResult()
     losses = torch.empty(steps, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
@@ -55,7 +56,7 @@ def fit(tex: Textures, batches, steps: int = 200, lr: float = 0.05, init=None) -
             n = diff.numel()
             losses[step] = diff.double().pow(2).sum() / n
             lookup_backward(tex, q, (2.0 / n) * diff, grad_texels=grad, flags=LOOKUP_BIN)
-            tex.adam_step(master, grad, m, v, step + 1, lr)
+            tex.adam_step(None, grad, m, v, step + 1, lr)
     torch.cuda.synchronize()
     res.seconds = time.perf_counter() - t0
     res.steps = steps

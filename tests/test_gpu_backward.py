@@ -150,6 +150,36 @@ def test_adam_step_matches_torch_adam():
         tex.adam_step(master, grad, m, v, 0, 0.01)
 
 
+def test_adam_step_in_place_on_the_pool():
+    """htex_textures_adam_step with no separate copy (master NULL): the
+    pool's own values follow torch.optim.Adam exactly as the master copy
+    does in the test above, and the gradient is cleared."""
+    fs, fv, V, _ = syn.uv_sphere(slices=8, rings=6, seed=2)
+    mesh = hx.Mesh(fs, fv, V)
+    log2n = (np.arange(mesh.E) % 4).astype(np.int32)
+    tot = int(sum(4 ** int(k) for k in log2n))
+    tex = hx.Textures.upload(mesh, log2n, np.zeros(tot * 3, np.float32), 3, "f32", hx.BUILD_MIPS)
+    n = tex.pool_elements
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    start = torch.randn(n, device="cuda", generator=gen)
+    tex.write_pool(start)
+    ref = start.clone().requires_grad_(True)
+    opt = torch.optim.Adam([ref], lr=0.02, betas=(0.9, 0.99), eps=1e-7)
+    grad = torch.zeros(n, device="cuda")
+    m, v = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    for step in range(1, 6):
+        g = torch.randn(n, device="cuda", generator=gen)
+        ref.grad = g.clone()
+        opt.step()
+        grad.copy_(g)
+        tex.adam_step(None, grad, m, v, step, 0.02, betas=(0.9, 0.99), eps=1e-7)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(grad) == 0
+        pool = torch.from_numpy(tex.download_pool()[0].view(np.float32).copy()).cuda()
+        assert torch.allclose(pool, ref.detach(), rtol=1e-5, atol=1e-6)
+
+
 U32 = 2.0 ** -24   # unit roundoff of float32
 
 

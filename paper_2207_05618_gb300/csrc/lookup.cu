@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const htex_query* q
 // ------------------------------------------ chunk-local sort (HTEX_LOOKUP_BIN)
 //
 // One chunk of m queries at a time: a bucket histogram, then per tile of
-// kSortTile queries a local counting sort in shared memory, so that every
+// kSortThreads x kSortPer queries (fewer per thread for wider queries or a
+// payload) a local counting sort in shared memory, so that every
 // bucket's run of the tile is written to the sorted copy as one contiguous
 // piece (whole sectors, not scattered 16-byte pieces), and each query's
 // sorted position is recorded in query order.  The lookup then filters the
@@ -138,7 +139,6 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_scatter(const htex_query* q
 
 constexpr int kSortThreads = 256;
 constexpr int kSortPer = 8;   // 16-byte query words per thread and tile (16: 8% slower sort, measured)
-constexpr int kSortTile = kSortThreads * kSortPer;
 constexpr int kSortMaxBuckets = 256;
 
 // QW: 16-byte words per query (1: htex_query, 2: htex_query_aniso); the

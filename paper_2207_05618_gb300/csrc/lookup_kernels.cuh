@@ -77,13 +77,16 @@ __device__ __forceinline__ void lookup_loop_pairs(const Asset<S>& A, const FwdPa
     }
 }
 
-// 2 resident blocks of 320 threads per SM (20 warps, 5 per scheduler) under
-// 102 registers: measured on the sorted asset batch against 2 x 256 (1.6%
-// slower), 2 x 384 and 3 x 256 (2.5-5% slower), 2 x 192 / 224 / 288 / 352
-// (slower; the odd warp counts leave the four schedulers uneven)
-constexpr int kGlobalThreads = 320;
+// One resident block of 640 threads per SM (20 warps, 5 per scheduler)
+// under 102 registers: each SM's threads then filter a contiguous stretch
+// of the (sorted) queries, so the texels of neighbouring queries meet in
+// its L1.  Measured on the sorted asset batch: 1 x 640 0.525 ms; 1 x 512,
+// 1 x 768 2-3% slower (1 x 896 and 1 x 1024 spill); 2 x 320 0.558 ms,
+// 2 x 256 1.6% slower than that, 2 x 384 and 3 x 256 2.5-5% slower, odd
+// warp counts per SM (2 x 224 / 288 / 352) slower still.
+constexpr int kGlobalThreads = 640;
 #ifndef HTEX_GLOBAL_MIN_BLOCKS
-#define HTEX_GLOBAL_MIN_BLOCKS 2
+#define HTEX_GLOBAL_MIN_BLOCKS 1
 #endif
 // one block of 1024 threads per SM (the pool staged once per SM): measured
 // against 384 x 3 / 512 x 2 / 576 x 2 / 640 x 2 blocks per SM, 2.3-4.6%

@@ -117,6 +117,45 @@ def test_sorted_backward_matches_unsorted_and_oracle():
     assert np.abs(c - ref[:c.shape[0]]).max() <= 1e-5 * max(np.abs(ref).max(), 1.0)
 
 
+@pytest.mark.parametrize("C,offsets", [(3, (0, 1, 2)), (2, (0, 2)), (1, (0, 1)), (4, (0,))])
+def test_backward_every_gradient_alignment(C, offsets):
+    """The adjoint into gradient buffers starting 16-, 8- and 4-byte aligned
+    (the widest atomics each allows: a float4 for a three-channel texel or a
+    pair of two-channel texels when 16-byte aligned, float2 pairs when
+    8-byte aligned, scalars otherwise), plain and sorted, on every
+    resolution 1..16 with trilinear footprints: each equals the FP64
+    oracle's gradient (1e-5 of its largest entry), and the elements before
+    and after the buffer stay untouched."""
+    gen = lambda: syn.uv_sphere(slices=12, rings=9, seed=3)
+    fs, fv, V, _ = gen()
+    mesh = hx.Mesh(fs, fv, V)
+    mo = oracle.mesh_from_faces(fs, fv, V)
+    log2n = (np.arange(mesh.E) * 7 % 5).astype(np.int32)
+    tex_np = syn.texels_f32(log2n, C, seed=40 + C)
+    tex = hx.Textures.upload(mesh, log2n, tex_np, C, "f32", hx.BUILD_MIPS)
+    to = oracle.prepare_textures(mo, log2n, tex_np, C, "f32", hx.BUILD_MIPS)
+    n = 30000
+    qs = syn.queries(mesh.H, n, seed=41, footprint="loguniform", lo=-5, hi=0.5)
+    g = np.random.default_rng(42).standard_normal((n, C)).astype(np.float32)
+    ref = oracle.grad_to_pool_layout(to, oracle.lookup_grad(mo, to, qs, g.astype(np.float64)), 4)
+    q = torch.from_numpy(hx.pack_queries(*qs)).cuda()
+    gd = torch.from_numpy(g).cuda()
+    m = tex.pool_elements
+    for off in offsets:
+        for flags in (0, hx.LOOKUP_BIN):
+            base = torch.full((m + 8,), 7.0, dtype=torch.float32, device="cuda")
+            grad = base[off:off + m]
+            grad.zero_()
+            assert grad.data_ptr() % 16 == 4 * off
+            hx.lookup_backward(tex, q, gd, grad_texels=grad, flags=flags)
+            torch.cuda.synchronize()
+            got = grad.double().cpu().numpy()
+            assert np.abs(got - ref).max() <= 1e-5 * max(np.abs(ref).max(), 1.0), (off, flags)
+            rest = torch.cat([base[:off], base[off + m:]]).cpu().numpy()
+            assert np.all(rest == 7.0), (off, flags)
+    tex.close()
+
+
 def test_adam_step_matches_torch_adam():
     """htex_textures_adam_step against torch.optim.Adam (plain PyTorch, the
     same hyper-parameters) over five steps of random gradients: the master

@@ -268,13 +268,13 @@ def mean_taps(he, n_uniform: int, qs, sample: int = 1 << 20) -> float:
 
 def algorithmic_bytes(taps: float, texel_bytes: int) -> dict:
     """Bytes one lookup must move on a one-resolution asset (no texture
-    headers), two ways.  'survey': the hot-path table's count -- the 16-byte
+    headers), two ways.  'hot_path': the hot-path table's count -- the 16-byte
     query, the 16-byte output, the 16-byte halfedge records of h, Next(h)
     and Prev(h), and the in-bounds taps.  'packed': this library's layout,
     where the three records are pre-evaluated into one 16-byte record of h
     (the same operators, evaluated at upload)."""
     tex = taps * texel_bytes
-    return {"survey": 16 + 16 + 3 * 16 + tex, "packed": 16 + 16 + 16 + tex, "taps": taps}
+    return {"hot_path": 16 + 16 + 3 * 16 + tex, "packed": 16 + 16 + 16 + tex, "taps": taps}
 
 
 # ------------------------------------------------------------------- clocks
@@ -565,9 +565,9 @@ def main():
     stages = {"filter_ms": avg_ms, "sort_and_gather_ms": float(np.mean(step_ms)) - avg_ms}
     rate = lambda b: b * nq / (avg_ms / 1e3) / 1e9
     traffic = profiled_traffic("lookup")
-    roofline = {"bound": "hbm", "achieved": rate(ab["survey"]), "peak": peak, "unit": "GB/s",
-                "frac": rate(ab["survey"]) / peak, "traffic": traffic, "peak_source": peak_src,
-                "algorithmic_bytes_per_lookup": ab["survey"],
+    roofline = {"bound": "hbm", "achieved": rate(ab["hot_path"]), "peak": peak, "unit": "GB/s",
+                "frac": rate(ab["hot_path"]) / peak, "traffic": traffic, "peak_source": peak_src,
+                "algorithmic_bytes_per_lookup": ab["hot_path"],
                 "definition": "algorithmic bytes of the hot-path table: 16 query + 16 output + 3 x 16 halfedge "
                               "records + 4 B per in-bounds tap of nonzero weight (mean taps counted on the "
                               "queries); no texture headers (one resolution)",

@@ -24,7 +24,7 @@ def _cube_halfedges():
 
 def test_algorithmic_bytes_definitions():
     ab = bench.algorithmic_bytes(6.5, 4)
-    assert ab["survey"] == 16 + 16 + 48 + 26.0       # query, output, three 16-byte records, taps
+    assert ab["hot_path"] == 16 + 16 + 48 + 26.0       # query, output, three 16-byte records, taps
     assert ab["packed"] == 16 + 16 + 16 + 26.0       # one pre-evaluated record
     assert ab["taps"] == 6.5
 
